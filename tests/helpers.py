@@ -1,0 +1,123 @@
+"""Test-only workload builders and transforms (no scheme arithmetic)."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from paper_1912_02457_gb300 import synth
+
+
+def flat(nx, ny, depth=100.0, dx=800.0, dy=800.0, f=0.0, theta=0.0, dtype=np.float64,
+         bc=(synth.BC_WALL,) * 4, **params):
+    z = np.zeros((ny, nx), dtype=dtype)
+    H = np.full((ny + 1, nx + 1), depth, dtype=dtype)
+    return synth.Workload(name=f"flat{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dy,
+                          eta=z.copy(), hu=z.copy(), hv=z.copy(), H=H,
+                          f=np.full((ny, nx), f, dtype=dtype),
+                          theta=np.full((ny, nx), theta, dtype=dtype),
+                          bc=tuple(bc), params=synth.Params(**params))
+
+
+def rough(nx, ny, seed=0, land=True, min_depth=None, dtype=np.float64, **kw):
+    """Small coastal-like domain: random bathymetry, land, varying f and theta,
+    walls on all sides (no forcing), for invariance tests."""
+    wl = synth.coastal(nx, ny, seed_config=90, member=seed,
+                       land_frac=0.3 if land else 0.0, dtype=np.float64)
+    wl.bc = (synth.BC_WALL,) * 4
+    wl.wind = None
+    wl.boundary = None
+    wl.params = synth.Params(**kw)
+    rng = np.random.default_rng(seed)
+    wl.f = (1.2e-4 + 2e-5 * rng.standard_normal((ny, nx)))
+    wl.theta = rng.uniform(-0.5, 0.5, (ny, nx))
+    if min_depth is not None:
+        Lm = wl.H == synth.LAND
+        wl.H = np.where(Lm, wl.H, np.maximum(wl.H, min_depth))
+        wl.eta = np.zeros((ny, nx))
+    if not land:
+        wl.H = np.where(wl.H == synth.LAND, 50.0, wl.H)
+    return wl.astype(dtype)
+
+
+def random_state(wl, seed=1, amp=0.3, mom=0.5):
+    rng = np.random.default_rng(seed)
+    ny, nx = wl.ny, wl.nx
+    land = wl.land_cells()
+    e = np.where(land, 0.0, amp * rng.standard_normal((ny, nx)))
+    u = np.where(land, 0.0, mom * rng.standard_normal((ny, nx)))
+    v = np.where(land, 0.0, mom * rng.standard_normal((ny, nx)))
+    return e, u, v
+
+
+# ---- symmetry transforms (state triples and workloads) -----------------------
+
+def flip_x_state(e, u, v):
+    return e[:, ::-1], -u[:, ::-1], v[:, ::-1]
+
+
+def flip_y_state(e, u, v):
+    return e[::-1, :], u[::-1, :], -v[::-1, :]
+
+
+def transpose_state(e, u, v):
+    return e.T, v.T, u.T
+
+
+def rot180_state(e, u, v):
+    return e[::-1, ::-1], -u[::-1, ::-1], -v[::-1, ::-1]
+
+
+def _wl_with(wl, **kw):
+    c = wl.copy()
+    for k, val in kw.items():
+        setattr(c, k, val)
+    return c
+
+
+def flip_x(wl):
+    S, N, W, E = wl.bc
+    return _wl_with(wl, H=wl.H[:, ::-1].copy(), f=-wl.f[:, ::-1].copy(),
+                    theta=-wl.theta[:, ::-1].copy(), bc=(S, N, E, W))
+
+
+def flip_y(wl):
+    S, N, W, E = wl.bc
+    return _wl_with(wl, H=wl.H[::-1, :].copy(), f=-wl.f[::-1, :].copy(),
+                    theta=(np.pi - wl.theta[::-1, :]).copy(), bc=(N, S, W, E))
+
+
+def transpose(wl):
+    S, N, W, E = wl.bc
+    return _wl_with(wl, nx=wl.ny, ny=wl.nx, dx=wl.dy, dy=wl.dx, H=wl.H.T.copy(),
+                    f=-wl.f.T.copy(), theta=(np.pi / 2 - wl.theta.T).copy(),
+                    bc=(W, E, S, N))
+
+
+def rot180(wl):
+    S, N, W, E = wl.bc
+    return _wl_with(wl, H=wl.H[::-1, ::-1].copy(), f=wl.f[::-1, ::-1].copy(),
+                    theta=(wl.theta[::-1, ::-1] + np.pi).copy(), bc=(N, S, E, W))
+
+
+def land_ring(wl, r=2):
+    """Embed a walled domain in an r-cell ring of land (corners of the ring
+    become LAND), keeping the domain's own walls outside the ring."""
+    nx, ny = wl.nx + 2 * r, wl.ny + 2 * r
+    H = np.full((ny + 1, nx + 1), synth.LAND, dtype=wl.H.dtype)
+    H[r:r + wl.ny + 1, r:r + wl.nx + 1] = wl.H
+
+    def pad(a, val=0.0):
+        out = np.full((ny, nx), val, dtype=a.dtype)
+        out[r:r + wl.ny, r:r + wl.nx] = a
+        return out
+
+    return _wl_with(wl, nx=nx, ny=ny, H=H, eta=pad(wl.eta), hu=pad(wl.hu), hv=pad(wl.hv),
+                    f=pad(wl.f, 1e-4), theta=pad(wl.theta))
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = max(np.abs(a).max(), np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / s)
