@@ -1,0 +1,190 @@
+/*
+ * swe.h -- C ABI of libswe, a GB300 (sm_103a) implementation of one time
+ * step of the well-balanced central-upwind finite-volume scheme for the
+ * rotating shallow-water equations of Brodtkorb & Holm, "Real-World
+ * Oceanographic Simulations on the GPU using a Two-Dimensional
+ * Finite-Volume Scheme" (arXiv 1912.02457).
+ *
+ * Every function returns SWE_OK (0) or a negative swe_status; none aborts
+ * and no C++ exception crosses the ABI. A handle may be used from one
+ * thread at a time; different handles may be used from different threads.
+ * All kernels of a domain run on the CUDA stream given at creation, in
+ * stream order, without host synchronisation unless a function says so.
+ *
+ * Grid conventions (Section 2): cell-average state (eta, hu, hv) on an
+ * nx x ny grid, row-major with x fastest; eta = h - H is the sea-surface
+ * deviation (eq:eta), hu and hv the momenta. The equilibrium depth H is
+ * given at the (nx+1) x (ny+1) cell corners and is piecewise bilinear
+ * (Section 3.9); a corner equal to SWE_LAND marks land (Section 3.4: the
+ * land mask is a no-data value of the bathymetry), and a cell with any
+ * SWE_LAND corner is land. Edges are numbered S, N, W, E = 0..3
+ * (S: j = 0, W: i = 0).
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWE_LAND 3.40282346638528859812e+38f  /* FLT_MAX: land corner */
+#define SWE_ABI_VERSION 1
+
+typedef enum {
+    SWE_OK = 0,
+    SWE_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum or ordering */
+    SWE_ERR_OOM = -2,          /* device or host allocation failed */
+    SWE_ERR_CUDA = -3,         /* a CUDA call failed; see swe_last_cuda_error */
+    SWE_ERR_NUMERIC = -4,      /* non-finite state or time step (sticky) */
+    SWE_ERR_UNSUPPORTED = -5   /* option not built into this library */
+} swe_status;
+
+typedef enum {
+    SWE_F32 = 0,        /* FP32 state and arithmetic */
+    SWE_F32_KAHAN = 1,  /* FP32 arithmetic, Kahan-compensated RK update */
+    SWE_F64 = 2         /* FP64 everywhere (parity build, not a fast path) */
+} swe_precision;
+
+typedef enum { SWE_BC_WALL = 0, SWE_BC_NESTED = 1 } swe_bc;
+typedef enum { SWE_FORCING_WIND = 0, SWE_FORCING_BOUNDARY = 1 } swe_forcing_kind;
+
+typedef enum {
+    SWE_ETA = 0, SWE_HU = 1, SWE_HV = 2,            /* state planes, nx*ny */
+    SWE_COMP_ETA = 3, SWE_COMP_HU = 4, SWE_COMP_HV = 5  /* Kahan terms */
+} swe_field;
+
+/* Scheme parameters (Sections 2-3). Fill with swe_default_params first. */
+typedef struct {
+    double g;               /* gravitational acceleration, 9.81 */
+    double theta_mm;        /* generalised-minmod parameter, 1.3 */
+    double kappa;           /* desingularisation depth of eq:desing_ours, 1e-2 m */
+    double cd;              /* quadratic bottom drag C_d (S = C_d |u| / |h*|) */
+    double courant;         /* Courant number of eq:cfl (dt = C/4 * min(...)) */
+    double frs_d0;          /* flow relaxation fall-off d0 of eq:frs, 2.5 */
+    int frs_width;          /* relaxation zone depth in cells (<= 32), 10 */
+    int dt_update_every;    /* recompute dt every k steps (Section 5), 1 */
+    double dt_fixed;        /* > 0: fixed dt, no CFL reduction */
+    double rho_air;         /* 1.225 (Section 3.5) */
+    double rho_water;       /* 1025 */
+    double t0;              /* initial simulated time, s */
+} swe_params;
+
+/* Domain description. Arrays are read once by swe_create_domain and
+ * copied; the caller keeps ownership. Element type of eta/hu/hv/H/f/theta
+ * is float for SWE_F32 and SWE_F32_KAHAN, double for SWE_F64. */
+typedef struct {
+    int nx, ny;             /* cells, 1 <= nx, ny <= 65536, nx*ny < 2^31;
+                               >= 2 across a nested edge */
+    double dx, dy;          /* cell size, m */
+    int precision;          /* swe_precision */
+    int bc[4];              /* swe_bc per edge S, N, W, E */
+    const void *eta, *hu, *hv;  /* nx*ny initial state */
+    const void *H;          /* (nx+1)*(ny+1) corner depths, SWE_LAND = land */
+    const void *f;          /* nx*ny Coriolis parameter, or NULL: f_const */
+    const void *theta;      /* nx*ny north angle (rad), or NULL: theta_const */
+    double f_const, theta_const;
+    int src_is_device;      /* 1: the pointers above are device pointers */
+} swe_domain_desc;
+
+typedef struct {
+    double t;               /* simulated time of the current state, s */
+    double dt;              /* time step the next step will take, s */
+    long long step;         /* steps taken since creation */
+    int error;              /* sticky swe_status of the device, 0 if none */
+    int error_cell;         /* first offending cell (j*nx+i), -1 if none */
+    long long error_step;   /* step at which it was found */
+    double max_speed;       /* last CFL reduction: max (|u|+c)/dx, (|v|+c)/dy */
+} swe_info;
+
+typedef struct swe_domain *swe_handle;
+
+/* Optional device allocator (e.g. a framework's caching allocator). When
+ * set, every device buffer of domains created afterwards comes from it and
+ * is returned to it by swe_destroy_domain. ctx is passed through. */
+typedef void *(*swe_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*swe_free_fn)(void *ptr, void *stream, void *ctx);
+int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn release, void *ctx);
+
+/* Defaults of the readings the paper leaves open: g = 9.81, theta = 1.3,
+ * kappa = 1e-2 m, C_d = 0, Courant 0.8 (Section 5), d0 = 2.5, zone 10
+ * cells, dt every step, rho_air 1.225, rho_water 1025, t0 = 0. */
+void swe_default_params(swe_params *p);
+
+/* Create a domain: validate the description, allocate its device planes,
+ * upload state and statics, and compute the first time step from the
+ * initial state by the CFL condition eq:cfl (Section 2), all on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).
+ * Errors: SWE_ERR_INVALID_ARG (sizes, enums, NULL pointers, frs_width),
+ * SWE_ERR_OOM, SWE_ERR_CUDA. On error *out is NULL and nothing leaks. */
+int swe_create_domain(const swe_domain_desc *d, const swe_params *p,
+                      void *stream, swe_handle *out);
+
+/* Set the forcing time series (Section 3.5 wind, Section 3.6 nesting).
+ * times: n_frames increasing host doubles (s); frames: host floats.
+ *   SWE_FORCING_WIND:     frames = n_frames x n2 x n1 x 2 wind at 10 m
+ *                         (grid axes, m/s) on an n1 x n2 grid spanning the
+ *                         domain, bilinear in space (cell centres),
+ *                         linear in time (eq:windstress_interpol).
+ *   SWE_FORCING_BOUNDARY: frames = n_frames x 12*(n1+n2): per frame edges
+ *                         S, N (n1 samples each) then W, E (n2 samples),
+ *                         each edge as [ghost row r][var v][k], r = 0 the
+ *                         ghost row touching the domain, v = eta, hu, hv;
+ *                         linear along the edge and in time; used by the
+ *                         ghost cells of nested edges and as Q^ext of the
+ *                         flow relaxation eq:frs.
+ * Outside [times[0], times[n-1]] the nearest frame is held. Data are
+ * copied (stream-ordered); the previous series is released after the
+ * stream reaches this call. Errors: SWE_ERR_INVALID_ARG, SWE_ERR_OOM. */
+int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times,
+                    const float *frames, int n1, int n2);
+
+/* Advance n_steps >= 0 steps of the semi-implicit SSP-RK2 scheme
+ * eq:rk2_semiimp with the central-upwind fluxes eqn:numerical_flux,
+ * asynchronously on the domain's stream. Each step: stage 1 at t, stage 2
+ * at t + dt, flow relaxation, then the fused CFL reduction sets the next
+ * dt on the device (no host synchronisation). Numerical failures are
+ * reported through swe_get_info / the next synchronising call.
+ * Errors: SWE_ERR_INVALID_ARG, SWE_ERR_CUDA (launch), SWE_ERR_NUMERIC
+ * (a sticky device error was already observed). */
+int swe_step(swe_handle h, int n_steps);
+
+/* Copy one field of the current state (nx*ny, row-major, element type of
+ * the domain's precision) to dst, host or device memory. Stream-ordered;
+ * for a host dst the call synchronises the stream before returning. */
+int swe_read_state(swe_handle h, int field, void *dst, int dst_is_device);
+
+/* Overwrite one field of the current state from src (same layout). Land
+ * cells keep whatever the caller writes. Writing a state field clears the
+ * matching Kahan term. Stream-ordered; the source must stay valid until
+ * the stream passes the call when src_is_device, and is copied before
+ * return for a host src. */
+int swe_write_state(swe_handle h, int field, const void *src, int src_is_device);
+
+/* Set the clock: time t, step counter, and dt (dt <= 0: recompute it from
+ * the current state by eq:cfl). Used to resume from a checkpoint. */
+int swe_set_clock(swe_handle h, double t, double dt, long long step);
+
+/* Synchronise the domain's stream and report clock, dt and the sticky
+ * device error (swe_info). Returns SWE_ERR_NUMERIC when a device error is
+ * set, SWE_ERR_CUDA when the stream failed. */
+int swe_get_info(swe_handle h, swe_info *out);
+
+/* Mass and energy over the wet cells, accumulated in FP64 on the device:
+ * out[0] = sum eta dx dy, out[1] = sum [(hu^2+hv^2)/(2|h*|) + g eta^2/2] dx dy.
+ * Synchronises the stream. */
+int swe_diagnostics(swe_handle h, double out[2]);
+
+/* Release every resource of the domain after its stream drains. */
+int swe_destroy_domain(swe_handle h);
+
+/* The last CUDA error string recorded by this thread, or "". */
+const char *swe_last_cuda_error(void);
+const char *swe_status_string(int status);
+int swe_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWE_H */

@@ -83,6 +83,9 @@ def lib():
                                   C.c_int, _dp]
             L.orc_diagnostics.restype = None
             L.orc_diagnostics.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, _dp, _dp]
+            L.orc_face_flux.restype = None
+            L.orc_face_flux.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
+                                        C.c_int, _dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -200,6 +203,14 @@ def wind_stress(wx, wy, rho_air=1.225, rho_water=1025.0):
     tx, ty = C.c_double(), C.c_double()
     lib().orc_wind_stress(wx, wy, rho_air, rho_water, C.byref(tx), C.byref(ty))
     return tx.value, ty.value
+
+
+def face_flux(left, right, Hf, dir, g=9.81, kappa=1e-2):
+    """Flux across one face from raw (h, eta, hu, hv) states on each side."""
+    a, b = _d(left), _d(right)
+    out = np.empty(3)
+    lib().orc_face_flux(_p(a), _p(b), float(Hf), g, kappa, int(dir), _p(out))
+    return out
 
 
 def num_threads():

@@ -204,8 +204,13 @@ typedef struct {
 #define KI(S, i, j) ((size_t)((j) + 2) * (S)->kx + (size_t)((i) + 2))
 
 /* Corner reflection about the boundary corner lines (reading: the
- * bathymetry continues evenly into the ghost region). */
-static int refl(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
+ * bathymetry continues evenly into the ghost region). Reflected again
+ * while outside, so that a domain one cell wide stays defined. */
+static int refl(int i, int n)
+{
+    while (i < 0 || i > n) i = i < 0 ? -i : 2 * n - i;
+    return i;
+}
 
 static void statics_free(statics *S)
 {
@@ -215,7 +220,10 @@ static void statics_free(statics *S)
 
 /* Mirror source cell of ghost cell (i, j) and the edge it belongs to, or -1
  * when (i, j) is interior or a ghost-ghost corner (unused by the plus-shaped
- * stencil). */
+ * stencil). The first ghost row mirrors the first interior row; the second
+ * mirrors the padded cell one further in, which is itself a ghost of the
+ * opposite edge when the domain is a single cell wide (so ghosts are filled
+ * row 1 on every edge before row 2). */
 static int ghost_source(int nx, int ny, int i, int j, int *si, int *sj, int *row)
 {
     int gx = (i < 0) || (i >= nx), gy = (j < 0) || (j >= ny);
@@ -269,24 +277,32 @@ static int statics_build(const orc_domain *d, statics *S)
             }
             int si, sj, row;
             int e = ghost_source(nx, ny, i, j, &si, &sj, &row);
-            double fv, th;
             if (e == -1) {
-                fv = d->f[(size_t)j * nx + i];
-                th = d->theta[(size_t)j * nx + i];
-            } else if (e == -2) {
-                fv = NAN; th = NAN;
+                S->f[c] = d->f[(size_t)j * nx + i];
+                S->ct[c] = d->theta[(size_t)j * nx + i];   /* angle for now */
             } else {
-                fv = d->f[(size_t)sj * nx + si];
-                th = d->theta[(size_t)sj * nx + si];
+                S->f[c] = NAN; S->ct[c] = NAN;
+            }
+        }
+    /* ghost f and angle, first ghost row of every edge, then the second */
+    for (int ring = 0; ring < 2; ring++)
+        for (int j = -2; j <= ny + 1; j++)
+            for (int i = -2; i <= nx + 1; i++) {
+                int si, sj, row;
+                int e = ghost_source(nx, ny, i, j, &si, &sj, &row);
+                if (e < 0 || row != ring) continue;
+                size_t c = CI(S, i, j), s = CI(S, si, sj);
                 /* Section 3.3: at a wall the Coriolis parameter is odd,
                  * f(-x) = -f(x), so that K_x = 0 across the wall. Nested
                  * edges continue f evenly (reading). */
-                if (d->bc[e] == ORC_WALL) fv = -fv;
+                S->f[c] = d->bc[e] == ORC_WALL ? -S->f[s] : S->f[s];
+                S->ct[c] = S->ct[s];
             }
-            S->f[c] = fv;
-            S->ct[c] = cos(th);
-            S->st[c] = sin(th);
-        }
+    for (size_t c = 0; c < (size_t)(nx + 4) * (ny + 4); c++) {
+        double th = S->ct[c];
+        S->ct[c] = cos(th);
+        S->st[c] = sin(th);
+    }
     return 0;
 }
 
@@ -298,6 +314,7 @@ static void fill_ghosts(const orc_domain *d, const statics *S,
                         double *eta, double *hu, double *hv, double t)
 {
     int nx = d->nx, ny = d->ny;
+    for (int ring = 0; ring < 2; ring++)
     for (int j = -2; j <= ny + 1; j++)
         for (int i = -2; i <= nx + 1; i++) {
             int si, sj, row;
@@ -305,6 +322,7 @@ static void fill_ghosts(const orc_domain *d, const statics *S,
             size_t c = CI(S, i, j);
             if (e == -1) continue;
             if (e == -2) { eta[c] = hu[c] = hv[c] = NAN; continue; }
+            if (row != ring) continue;
             size_t s = CI(S, si, sj);
             if (d->bc[e] == ORC_WALL) {
                 eta[c] = eta[s];
@@ -352,9 +370,17 @@ static void cu_flux(face L, face R, double Hf, double g, int dir, double out[3])
     double unL = dir == 0 ? L.u : L.v, unR = dir == 0 ? R.u : R.v;
     double ap = fmax(fmax(unL + L.c, unR + R.c), 0.0);
     double am = fmin(fmin(unL - L.c, unR - R.c), 0.0);
-    if (ap - am == 0.0) { out[0] = out[1] = out[2] = 0.0; return; }
     double pL = 0.5 * g * L.eta * (L.eta + 2.0 * Hf);
     double pR = 0.5 * g * R.eta * (R.eta + 2.0 * Hf);
+    if (ap - am == 0.0) {
+        /* a+ = a- = 0 only between two dry faces at rest; there the h-form
+         * flux is zero, which in eta variables is the pressure
+         * -g H_f^2 / 2 (= pL = pR) in the normal momentum. */
+        out[0] = 0.0;
+        out[1] = dir == 0 ? pL : 0.0;
+        out[2] = dir == 0 ? 0.0 : pL;
+        return;
+    }
     double FL[3], FR[3];
     if (dir == 0) {
         FL[0] = L.hu; FL[1] = L.hu * L.u + pL; FL[2] = L.hu * L.v;
@@ -645,6 +671,17 @@ int orc_rhs(const orc_domain *d, const double *eta, const double *hu,
     work_free(&W);
     statics_free(&S);
     return 0;
+}
+
+/* One face flux from raw face states (h, eta, hu, hv) on both sides, the
+ * face depth H_f and the direction: desingularised and combined exactly as
+ * in the right-hand side (exported for the eta-form vs h-form test). */
+void orc_face_flux(const double *left, const double *right, double Hf, double g,
+                   double kappa, int dir, double *out)
+{
+    raw_face a = { left[0], left[1], left[2], left[3] };
+    raw_face b = { right[0], right[1], right[2], right[3] };
+    cu_flux(finish_face(a, g, kappa), finish_face(b, g, kappa), Hf, g, dir, out);
 }
 
 /* Face values of the x-reconstruction of every interior cell (eta^E, eta^W,

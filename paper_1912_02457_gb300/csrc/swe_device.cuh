@@ -1,0 +1,233 @@
+// swe_device.cuh -- per-cell arithmetic of the well-balanced central-upwind
+// scheme (Brodtkorb & Holm, arXiv 1912.02457), shared by every stage kernel
+// of libswe. Templated on the arithmetic type T (float or double).
+#pragma once
+
+#include "swe_internal.h"
+
+namespace swe {
+
+// Desingularised depth, eq:desing_ours (Section 3.2):
+// h* = sign(h) max(|h|, min(h^2/(2 kappa) + kappa/2, kappa)), sign(0) = +1.
+template <typename T>
+__device__ __forceinline__ T desing(T h, T kappa, T half_inv_kappa) {
+    T m = fmin(h * h * half_inv_kappa + T(0.5) * kappa, kappa);
+    T r = fmax(fabs(h), m);
+    return h < T(0) ? -r : r;
+}
+
+// Generalised minmod of (theta*backward, central, theta*forward).
+template <typename T>
+__device__ __forceinline__ T minmod3(T a, T b, T c) {
+    if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
+    if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
+    return T(0);
+}
+
+// One cell as seen by the stencil: state, bilinear bathymetry at the cell
+// average and face midpoints, Coriolis parameter and north angle, and the
+// derived primitives of the reconstruction.
+template <typename T>
+struct Cell {
+    bool land;
+    T eta, hu, hv;
+    T Hbar, HE, HW, HN, HS;
+    T f, ct, st;
+    T hbar, hs, u, v;
+    T fvx, fuy;        // f x.[v^n,-u^e] and -f y.[v^n,-u^e] (Section 3.7)
+};
+
+// Face state before (raw) and after desingularisation.
+template <typename T>
+struct Face {
+    T h, eta, hu, hv, u, v, c;
+};
+
+// Cell averages and north-vector-projected Coriolis terms (Sections 3.1,
+// 3.2 and 3.7): hbar = eta + Hbar, u = hu/h*, v = hv/h*,
+// u^e = e.[u,v], v^n = n.[u,v] with e = [cos,-sin], n = [sin,cos];
+// the x-reconstruction uses f x.[v^n,-u^e] (= f v), the y-reconstruction
+// -f y.[v^n,-u^e] (= f u), with x = [cos, sin] and y = [-sin, cos].
+template <typename T>
+__device__ __forceinline__ void make_prim(Cell<T> &c, T kappa, T hik) {
+    c.hbar = c.eta + c.Hbar;
+    c.hs = desing(c.hbar, kappa, hik);
+    T r = T(1) / c.hs;
+    c.u = c.hu * r;
+    c.v = c.hv * r;
+    T ue = c.ct * c.u - c.st * c.v;
+    T vn = c.st * c.u + c.ct * c.v;
+    T xs = c.ct * vn - c.st * ue;
+    T ys = -c.st * vn - c.ct * ue;
+    c.fvx = c.f * xs;
+    c.fuy = -c.f * ys;
+}
+
+// Reconstruction of the centre cell `c` along x (DIR 0) or y (DIR 1),
+// Section 3.1 in its local form (eq:Kbackwards, eq:hE): with
+// phi = (dx/2g) f v (x) or -(dy/2g) f u (y),
+//   bw = (eta_c - eta_l) - (phi_l + phi_c), fw = (eta_r - eta_c) - (phi_c + phi_r),
+//   s  = minmod(theta bw, (bw+fw)/2, theta fw),
+//   eta+ = eta_c + s/2 + phi_c, eta- = eta_c - s/2 - phi_c.
+// Land neighbours are the mirror of the centre cell (Section 3.4).
+// Wet-dry (eq:KxE_adjust): a negative face is re-sloped to zero depth and
+// the other face gets 2 hbar; a cell with hbar <= 0 is dry on both faces.
+// Momentum faces: minmod-limited slopes of hu and hv.
+template <typename T, int DIR>
+__device__ __forceinline__ void reconstruct(const Cell<T> &l, const Cell<T> &c,
+                                            const Cell<T> &r, T k, T tm,
+                                            Face<T> &plus, Face<T> &minus) {
+    const T sg = DIR == 0 ? T(1) : T(-1);
+    T phc = sg * k * (DIR == 0 ? c.fvx : c.fuy);
+    T el, ml1, ml2, phl, er, mr1, mr2, phr;
+    if (l.land) {
+        el = c.eta; phl = -phc;
+        ml1 = DIR == 0 ? -c.hu : c.hu;
+        ml2 = DIR == 0 ? c.hv : -c.hv;
+    } else {
+        el = l.eta; ml1 = l.hu; ml2 = l.hv;
+        phl = sg * k * (DIR == 0 ? l.fvx : l.fuy);
+    }
+    if (r.land) {
+        er = c.eta; phr = -phc;
+        mr1 = DIR == 0 ? -c.hu : c.hu;
+        mr2 = DIR == 0 ? c.hv : -c.hv;
+    } else {
+        er = r.eta; mr1 = r.hu; mr2 = r.hv;
+        phr = sg * k * (DIR == 0 ? r.fvx : r.fuy);
+    }
+    T bw = (c.eta - el) - (phl + phc);
+    T fw = (er - c.eta) - (phc + phr);
+    T sK = minmod3(tm * bw, T(0.5) * (bw + fw), tm * fw);
+    T b1 = c.hu - ml1, f1 = mr1 - c.hu;
+    T s1 = minmod3(tm * b1, T(0.5) * (b1 + f1), tm * f1);
+    T b2 = c.hv - ml2, f2 = mr2 - c.hv;
+    T s2 = minmod3(tm * b2, T(0.5) * (b2 + f2), tm * f2);
+
+    T Hp = DIR == 0 ? c.HE : c.HN;
+    T Hm = DIR == 0 ? c.HW : c.HS;
+    T etap = c.eta + T(0.5) * sK + phc;
+    T etam = c.eta - T(0.5) * sK - phc;
+    T hp = etap + Hp, hm = etam + Hm;
+    if (c.hbar <= T(0)) {
+        etap = -Hp; etam = -Hm; hp = T(0); hm = T(0);
+    } else if (hp < T(0)) {
+        etap = -Hp; hp = T(0);
+        etam = T(2) * c.eta + Hp; hm = etam + Hm;
+    } else if (hm < T(0)) {
+        etam = -Hm; hm = T(0);
+        etap = T(2) * c.eta + Hm; hp = etap + Hp;
+    }
+    plus.h = fmax(hp, T(0));  plus.eta = etap;
+    minus.h = fmax(hm, T(0)); minus.eta = etam;
+    plus.hu = c.hu + T(0.5) * s1;  minus.hu = c.hu - T(0.5) * s1;
+    plus.hv = c.hv + T(0.5) * s2;  minus.hv = c.hv - T(0.5) * s2;
+}
+
+// Desingularised face velocities; face momenta reset to h u, h v so that a
+// dry face carries none; gravity-wave speed sqrt(g h).
+template <typename T>
+__device__ __forceinline__ void finish_face(Face<T> &F, T g, T kappa, T hik) {
+    T hs = desing(F.h, kappa, hik);
+    T r = T(1) / hs;
+    F.u = F.hu * r;
+    F.v = F.hv * r;
+    F.hu = F.h * F.u;
+    F.hv = F.h * F.v;
+    F.c = sqrt(g * F.h);
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ Face<T> mirror(Face<T> F) {
+    if (DIR == 0) { F.hu = -F.hu; F.u = -F.u; }
+    else          { F.hv = -F.hv; F.v = -F.v; }
+    return F;
+}
+
+// Central-upwind flux eqn:numerical_flux in the eta variables (pressure
+// g eta (eta + 2 H_f)/2; the constant g H_f^2/2 of the h form cancels
+// against the matching part of the bed term). out = flux along DIR.
+template <typename T, int DIR>
+__device__ __forceinline__ void cu_flux(const Face<T> &L, const Face<T> &R, T Hf, T g,
+                                        T out[3]) {
+    T unL = DIR == 0 ? L.u : L.v, unR = DIR == 0 ? R.u : R.v;
+    T ap = fmax(fmax(unL + L.c, unR + R.c), T(0));
+    T am = fmin(fmin(unL - L.c, unR - R.c), T(0));
+    T den = ap - am;
+    T pL = T(0.5) * g * L.eta * (L.eta + T(2) * Hf);
+    T pR = T(0.5) * g * R.eta * (R.eta + T(2) * Hf);
+    if (den == T(0)) {
+        // two dry faces at rest: the h-form flux is zero, i.e. the eta-form
+        // normal momentum flux is the dry pressure -g H_f^2/2 (= pL = pR)
+        out[0] = T(0);
+        out[1] = DIR == 0 ? pL : T(0);
+        out[2] = DIR == 0 ? T(0) : pL;
+        return;
+    }
+    T rd = T(1) / den;
+    T FL0, FL1, FL2, FR0, FR1, FR2;
+    if (DIR == 0) {
+        FL0 = L.hu; FL1 = L.hu * L.u + pL; FL2 = L.hu * L.v;
+        FR0 = R.hu; FR1 = R.hu * R.u + pR; FR2 = R.hu * R.v;
+    } else {
+        FL0 = L.hv; FL1 = L.hv * L.u; FL2 = L.hv * L.v + pL;
+        FR0 = R.hv; FR1 = R.hv * R.u; FR2 = R.hv * R.v + pR;
+    }
+    T apam = ap * am;
+    out[0] = (ap * FL0 - am * FR0 + apam * (R.eta - L.eta)) * rd;
+    out[1] = (ap * FL1 - am * FR1 + apam * (R.hu - L.hu)) * rd;
+    out[2] = (ap * FL2 - am * FR2 + apam * (R.hv - L.hv)) * rd;
+}
+
+// Large & Pond wind stress (Section 3.5).
+template <typename T>
+__device__ __forceinline__ void wind_stress(T wx, T wy, T rho_ratio, T &tx, T &ty) {
+    T w = sqrt(wx * wx + wy * wy);
+    T cdrag = (w < T(11)) ? T(1.2e-3) : (T(0.49) + T(0.065) * w) * T(1e-3);
+    T k = rho_ratio * cdrag * w;
+    tx = k * wx;
+    ty = k * wy;
+}
+
+// Kahan-compensated s += x; the represented value is s - c.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &s, T &c, T x) {
+    T y = x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Texture-like sampling position of cell k of n on nb samples.
+__device__ __forceinline__ void axis_pos(int k, int n, int nb, int &k0, int &k1, double &w) {
+    double p = (k + 0.5) * (double)nb / (double)n - 0.5;
+    p = fmin(fmax(p, 0.0), (double)(nb - 1));
+    int a = (int)floor(p);
+    if (a > nb - 1) a = nb - 1;
+    k0 = a;
+    k1 = a + 1 < nb ? a + 1 : nb - 1;
+    w = p - a;
+}
+
+// External solution of edge e, ghost row r, variable v at along-edge cell k,
+// interpolated along the edge and in time with the stage's frame bracket.
+template <typename T>
+__device__ T bnd_value(const StageArgs<T> &a, int e, int r, int v, int k, int stage) {
+    const ForcingDev &F = a.bnd;
+    int nb = e < 2 ? F.n1 : F.n2;
+    int n = e < 2 ? a.nx : a.ny;
+    long long off = (e >= 1 ? 6LL * F.n1 : 0) + (e >= 2 ? 6LL * F.n1 : 0) + (e >= 3 ? 6LL * F.n2 : 0);
+    int k0, k1;
+    double w;
+    axis_pos(k, n, nb, k0, k1, w);
+    int fk = a.ctl->bk[stage];
+    double s = a.ctl->bs[stage];
+    long long fs = 12LL * (F.n1 + F.n2);
+    const float *A = F.frames + (long long)fk * fs + off + (long long)(r * 3 + v) * nb;
+    const float *B = F.n > 1 ? A + fs : A;
+    double va = (1.0 - w) * A[k0] + w * A[k1];
+    double vb = (1.0 - w) * B[k0] + w * B[k1];
+    return T((1.0 - s) * va + s * vb);
+}
+
+}  // namespace swe

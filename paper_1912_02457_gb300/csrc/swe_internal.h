@@ -1,0 +1,76 @@
+// swe_internal.h -- device-side data structures shared by the kernels and
+// the C-ABI host code of libswe. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swe {
+
+constexpr int kMaxFrs = 32;          // deepest flow-relaxation zone supported
+constexpr float kLand = 3.40282346638528859812e+38f;  // FLT_MAX corner marker
+enum { EDGE_S = 0, EDGE_N = 1, EDGE_W = 2, EDGE_E = 3 };
+enum { BC_WALL = 0, BC_NESTED = 1 };
+enum { ERR_NONE = 0, ERR_NUMERIC = -4 };
+
+// Device-resident clock of one domain. The stage kernels read dt and the
+// forcing brackets from here and the end-of-step reduction writes the next
+// dt here, so a sequence of steps needs no host round trip.
+struct StepCtl {
+    double t;                 // simulated time of the current state
+    double dt;                // dt of the next step
+    long long step;           // steps taken
+    double tau[2][2];         // uniform wind stress at stage-1 / stage-2 time
+    double bs[2];             // boundary frame weight s at stage-1 / stage-2 time
+    double ws[2];             // wind frame weight s
+    int bk[2];                // boundary frame index at stage-1 / stage-2 time
+    int wk[2];                // wind frame index
+    double last_speed;        // last CFL reduction result
+    unsigned int speed32;     // atomicMax target (float bits)
+    unsigned int blocks_done; // last-block-done counter of the fused finalise
+    unsigned long long speed64;  // atomicMax target (double bits)
+    int err;                  // sticky error code
+    int err_cell;             // first offending cell, -1 if none
+    long long err_step;
+};
+
+// Clock policy, copied by value into the finalise kernels.
+struct ClockParams {
+    double courant;
+    double dt_fixed;
+    int dt_every;
+    int wind_uniform;         // wind frames are 1x1: precompute tau per stage
+    double rho_ratio;         // rho_air / rho_water
+};
+
+struct ForcingDev {
+    const float *frames;      // device frames (layout in swe.h)
+    const double *times;      // device times
+    int n, n1, n2;            // frames, samples along x / y (or grid size)
+};
+
+template <typename T>
+struct StageArgs {
+    int nx, ny;
+    long long pitch;          // elements per row of cell planes
+    long long cpitch;         // elements per row of the corner plane
+    T dx, dy, inv_dx, inv_dy;
+    T kx, ky;                 // dx/(2g), dy/(2g)
+    T g, kappa, half_inv_kappa, tm, cd;
+    int bc[4];
+    const T *H, *f, *th;      // corner depths; f/theta planes or NULL
+    T f_const, th_const;
+    const T *qin[3];          // state at the start of the step
+    T *qout[3];               // state after the step (stage 2)
+    T *d1[3];                 // stage-1 increment Q* - Q^n
+    T *comp[3];               // Kahan compensation (F32_KAHAN) or NULL
+    ForcingDev bnd, wind;
+    int frs_width;
+    double frs_alpha[kMaxFrs];
+    StepCtl *ctl;
+    ClockParams clk;
+    float *partials;          // per-block maxima of the fused finalise
+    int nblocks;              // blocks of the stage-2 launch
+};
+
+}  // namespace swe

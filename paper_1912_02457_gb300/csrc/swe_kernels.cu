@@ -1,0 +1,494 @@
+// swe_kernels.cu -- stage, reduction, clock and diagnostic kernels of libswe.
+//
+// One time step is two launches of the stage kernel (eq:rk2_semiimp) and a
+// one-thread clock kernel:
+//   stage 1: M(Q^n), S(Q^n) at time t        -> D1 = Q* - Q^n
+//   stage 2: M(Q*),  S(Q*)  at time t + dt   -> Q^{n+1}, flow relaxation,
+//            block-max of the CFL wave speed (atomicMax into the clock)
+//   clock:   t += dt, next dt from the max speed (eq:cfl), forcing brackets.
+// The reference stage kernel here maps one thread to one cell and reads its
+// radius-2 plus-shaped stencil straight from global memory.
+#include "swe_device.cuh"
+#include "swe_kernels.h"
+
+namespace swe {
+
+// ---------------------------------------------------------------------------
+// stencil loads
+
+template <typename T>
+__device__ __forceinline__ void sincos_t(T x, T *s, T *c);
+template <>
+__device__ __forceinline__ void sincos_t<float>(float x, float *s, float *c) { sincosf(x, s, c); }
+template <>
+__device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c) { sincos(x, s, c); }
+
+// Cell (i, j) of the stencil, i and j possibly one or two cells outside the
+// domain. Outside a wall edge the cell is land (a wall is the land-mask
+// wall of Section 3.4, which equals the ghost mirror of Section 3.3).
+// Outside a nested edge it is a ghost cell: bathymetry, f and theta of the
+// mirrored interior cell (faces swapped), state from the external frames
+// at the stage time (Section 3.6).
+template <typename T, int STAGE>
+__device__ __forceinline__ void load_cell(const StageArgs<T> &a, int i, int j, Cell<T> &c) {
+    const int nx = a.nx, ny = a.ny;
+    int si = i, sj = j, e = -1, row = 0;
+    if (i < 0)        { e = EDGE_W; si = -i - 1;         row = -i - 1; }
+    else if (i >= nx) { e = EDGE_E; si = 2 * nx - 1 - i; row = i - nx; }
+    else if (j < 0)   { e = EDGE_S; sj = -j - 1;         row = -j - 1; }
+    else if (j >= ny) { e = EDGE_N; sj = 2 * ny - 1 - j; row = j - ny; }
+    if (e >= 0 && a.bc[e] == BC_WALL) { c.land = true; return; }
+    const long long cp = a.cpitch;
+    const T *H = a.H + (long long)sj * cp + si;
+    T c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];
+    const T L = T(kLand);
+    c.land = (c00 == L) | (c10 == L) | (c01 == L) | (c11 == L);
+    if (c.land) return;
+    c.Hbar = T(0.25) * (c00 + c10 + c01 + c11);
+    T HE = T(0.5) * (c10 + c11), HW = T(0.5) * (c00 + c01);
+    T HN = T(0.5) * (c01 + c11), HS = T(0.5) * (c00 + c10);
+    if (e == EDGE_W || e == EDGE_E) { T t = HE; HE = HW; HW = t; }
+    if (e == EDGE_S || e == EDGE_N) { T t = HN; HN = HS; HS = t; }
+    c.HE = HE; c.HW = HW; c.HN = HN; c.HS = HS;
+    const long long s = (long long)sj * a.pitch + si;
+    c.f = a.f ? a.f[s] : a.f_const;
+    T th = a.th ? a.th[s] : a.th_const;
+    sincos_t(th, &c.st, &c.ct);
+    if (e < 0) {
+        c.eta = a.qin[0][s]; c.hu = a.qin[1][s]; c.hv = a.qin[2][s];
+        if (STAGE == 2) { c.eta += a.d1[0][s]; c.hu += a.d1[1][s]; c.hv += a.d1[2][s]; }
+    } else {
+        int k = e >= EDGE_W ? j : i;
+        c.eta = bnd_value(a, e, row, 0, k, STAGE - 1);
+        c.hu = bnd_value(a, e, row, 1, k, STAGE - 1);
+        c.hv = bnd_value(a, e, row, 2, k, STAGE - 1);
+    }
+    make_prim(c, a.kappa, a.half_inv_kappa);
+}
+
+__device__ __forceinline__ void axis_pos_f(int k, int n, int nb, int &k0, int &k1, float &w) {
+    float p = (k + 0.5f) * (float)nb / (float)n - 0.5f;
+    p = fminf(fmaxf(p, 0.0f), (float)(nb - 1));
+    int q = (int)floorf(p);
+    if (q > nb - 1) q = nb - 1;
+    k0 = q;
+    k1 = q + 1 < nb ? q + 1 : nb - 1;
+    w = p - q;
+}
+
+// Wind stress at cell (i, j) at the stage time (Section 3.5): uniform
+// frames use the stress the clock kernel computed in FP64; gridded frames
+// are sampled bilinearly at the cell centre and lerped in time here.
+template <typename T>
+__device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int stage,
+                                        T rho_ratio, T &tx, T &ty) {
+    if (a.wind.n <= 0) { tx = T(0); ty = T(0); return; }
+    if (a.clk.wind_uniform) {
+        tx = T(a.ctl->tau[stage][0]);
+        ty = T(a.ctl->tau[stage][1]);
+        return;
+    }
+    const ForcingDev &F = a.wind;
+    int x0, x1, y0, y1;
+    float wx, wy;
+    axis_pos_f(i, a.nx, F.n1, x0, x1, wx);
+    axis_pos_f(j, a.ny, F.n2, y0, y1, wy);
+    int fk = a.ctl->wk[stage];
+    float s = (float)a.ctl->ws[stage];
+    long long fs = 2LL * F.n1 * F.n2;
+    const float *A = F.frames + fk * fs;
+    const float *B = F.n > 1 ? A + fs : A;
+    float W[2];
+    for (int c = 0; c < 2; c++) {
+        float a0 = (1.f - wx) * A[(y0 * F.n1 + x0) * 2 + c] + wx * A[(y0 * F.n1 + x1) * 2 + c];
+        float a1 = (1.f - wx) * A[(y1 * F.n1 + x0) * 2 + c] + wx * A[(y1 * F.n1 + x1) * 2 + c];
+        float b0 = (1.f - wx) * B[(y0 * F.n1 + x0) * 2 + c] + wx * B[(y0 * F.n1 + x1) * 2 + c];
+        float b1 = (1.f - wx) * B[(y1 * F.n1 + x0) * 2 + c] + wx * B[(y1 * F.n1 + x1) * 2 + c];
+        W[c] = (1.f - s) * ((1.f - wy) * a0 + wy * a1) + s * ((1.f - wy) * b0 + wy * b1);
+    }
+    wind_stress<T>(T(W[0]), T(W[1]), rho_ratio, tx, ty);
+}
+
+// ---------------------------------------------------------------------------
+// block reductions
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T *sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        v = tid < nw ? sh[tid] : T(0);
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
+__device__ __forceinline__ void speed_atomic_max(StepCtl *ctl, float v) {
+    atomicMax(&ctl->speed32, __float_as_uint(v));
+}
+__device__ __forceinline__ void speed_atomic_max(StepCtl *ctl, double v) {
+    atomicMax(&ctl->speed64, (unsigned long long)__double_as_longlong(v));
+}
+
+// CFL wave speed of one cell, eq:cfl: max((|u| + sqrt(g hbar+))/dx,
+// (|v| + sqrt(g hbar+))/dy) with desingularised cell velocities.
+template <typename T>
+__device__ __forceinline__ T cell_speed(const StageArgs<T> &a, T eta, T hu, T hv, T Hbar) {
+    T hbar = eta + Hbar;
+    T hs = desing(hbar, a.kappa, a.half_inv_kappa);
+    T c = sqrt(a.g * fmax(hbar, T(0)));
+    T r = T(1) / hs;
+    T sx = (fabs(hu * r) + c) * a.inv_dx;
+    T sy = (fabs(hv * r) + c) * a.inv_dy;
+    return fmax(sx, sy);
+}
+
+__device__ __forceinline__ void flag_error(StepCtl *ctl, int cell) {
+    if (atomicCAS(&ctl->err_cell, -1, cell) == -1) {
+        ctl->err = ERR_NUMERIC;
+        ctl->err_step = ctl->step;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the reference stage kernel: one thread per cell
+
+template <typename T, int STAGE, bool KAHAN>
+__global__ void __launch_bounds__(256) stage_ref_kernel(StageArgs<T> a) {
+    __shared__ T sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool act = i < a.nx && j < a.ny;
+    T speed = T(0);
+    Cell<T> C;
+    C.land = true;
+    if (act) load_cell<T, STAGE>(a, i, j, C);
+    if (act && !C.land) {
+        const T g = a.g, kappa = a.kappa, hik = a.half_inv_kappa;
+        Cell<T> W2, W1, E1, E2, S2, S1, N1, N2;
+        load_cell<T, STAGE>(a, i - 2, j, W2);
+        load_cell<T, STAGE>(a, i - 1, j, W1);
+        load_cell<T, STAGE>(a, i + 1, j, E1);
+        load_cell<T, STAGE>(a, i + 2, j, E2);
+        load_cell<T, STAGE>(a, i, j - 2, S2);
+        load_cell<T, STAGE>(a, i, j - 1, S1);
+        load_cell<T, STAGE>(a, i, j + 1, N1);
+        load_cell<T, STAGE>(a, i, j + 2, N2);
+
+        Face<T> cE, cW, cN, cS, L, R;
+        T Fw[3], Fe[3], Gs[3], Gn[3];
+        reconstruct<T, 0>(W1, C, E1, a.kx, a.tm, cE, cW);
+        reconstruct<T, 1>(S1, C, N1, a.ky, a.tm, cN, cS);
+        const T etaE = cE.eta, etaW = cW.eta, etaN = cN.eta, etaS = cS.eta;
+        // west face
+        R = cW; finish_face(R, g, kappa, hik);
+        if (W1.land) L = mirror<T, 0>(R);
+        else { Face<T> p, m; reconstruct<T, 0>(W2, W1, C, a.kx, a.tm, p, m); L = p; finish_face(L, g, kappa, hik); }
+        cu_flux<T, 0>(L, R, C.HW, g, Fw);
+        // east face
+        L = cE; finish_face(L, g, kappa, hik);
+        if (E1.land) R = mirror<T, 0>(L);
+        else { Face<T> p, m; reconstruct<T, 0>(C, E1, E2, a.kx, a.tm, p, m); R = m; finish_face(R, g, kappa, hik); }
+        cu_flux<T, 0>(L, R, C.HE, g, Fe);
+        // south face
+        R = cS; finish_face(R, g, kappa, hik);
+        if (S1.land) L = mirror<T, 1>(R);
+        else { Face<T> p, m; reconstruct<T, 1>(S2, S1, C, a.ky, a.tm, p, m); L = p; finish_face(L, g, kappa, hik); }
+        cu_flux<T, 1>(L, R, C.HS, g, Gs);
+        // north face
+        L = cN; finish_face(L, g, kappa, hik);
+        if (N1.land) R = mirror<T, 1>(L);
+        else { Face<T> p, m; reconstruct<T, 1>(C, N1, N2, a.ky, a.tm, p, m); R = m; finish_face(R, g, kappa, hik); }
+        cu_flux<T, 1>(L, R, C.HN, g, Gn);
+
+        // M(Q) = -dF/dx - dG/dy + B + C + W (eq:sw_semidiscrete)
+        T m0 = -(Fe[0] - Fw[0]) * a.inv_dx - (Gn[0] - Gs[0]) * a.inv_dy;
+        T m1 = -(Fe[1] - Fw[1]) * a.inv_dx - (Gn[1] - Gs[1]) * a.inv_dy;
+        T m2 = -(Fe[2] - Fw[2]) * a.inv_dx - (Gn[2] - Gs[2]) * a.inv_dy;
+        m1 += g * T(0.5) * (etaE + etaW) * (C.HE - C.HW) * a.inv_dx;   // bed, eta form
+        m2 += g * T(0.5) * (etaN + etaS) * (C.HN - C.HS) * a.inv_dy;
+        T hue = C.ct * C.hu - C.st * C.hv;                               // Coriolis
+        T hvn = C.st * C.hu + C.ct * C.hv;
+        m1 += C.f * (C.ct * hvn - C.st * hue);
+        m2 += C.f * (-C.st * hvn - C.ct * hue);
+        T tx, ty;
+        wind_at(a, i, j, STAGE - 1, T(a.clk.rho_ratio), tx, ty);
+        m1 += tx;
+        m2 += ty;
+        T S = a.cd * sqrt(C.u * C.u + C.v * C.v) / fabs(C.hs);          // drag rate
+
+        const T dt = T(a.ctl->dt);
+        const long long s = (long long)j * a.pitch + i;
+        if (STAGE == 1) {
+            T den = T(1) / (T(1) + dt * S);
+            a.d1[0][s] = dt * m0;
+            a.d1[1][s] = (dt * m1 - dt * S * C.hu) * den;
+            a.d1[2][s] = (dt * m2 - dt * S * C.hv) * den;
+        } else {
+            // Q^{n+1} - Q^n = (D1 + dt M(Q*) - dt S Q^n) / 2 / (1 + dt S / 2)
+            T q0 = a.qin[0][s], q1 = a.qin[1][s], q2 = a.qin[2][s];
+            T D0 = a.d1[0][s], D1 = a.d1[1][s], D2 = a.d1[2][s];
+            T den = T(1) / (T(1) + T(0.5) * dt * S);
+            T de0 = T(0.5) * (D0 + dt * m0);
+            T de1 = T(0.5) * (D1 + dt * m1 - dt * S * q1) * den;
+            T de2 = T(0.5) * (D2 + dt * m2 - dt * S * q2) * den;
+            T c0 = 0, c1 = 0, c2 = 0;
+            if (KAHAN) {
+                c0 = a.comp[0][s]; c1 = a.comp[1][s]; c2 = a.comp[2][s];
+                kahan_add(q0, c0, de0);
+                kahan_add(q1, c1, de1);
+                kahan_add(q2, c2, de2);
+            } else {
+                q0 += de0; q1 += de1; q2 += de2;
+            }
+            // flow relaxation, eq:frs, nested edges in the order S, N, W, E
+            for (int e = 0; e < 4; e++) {
+                if (a.bc[e] != BC_NESTED) continue;
+                int d = e == EDGE_S ? j : e == EDGE_N ? a.ny - 1 - j : e == EDGE_W ? i : a.nx - 1 - i;
+                if (d >= a.frs_width) continue;
+                int k = e >= EDGE_W ? j : i;
+                T al = T(a.frs_alpha[d]);
+                T x0 = bnd_value(a, e, 0, 0, k, 1), x1 = bnd_value(a, e, 0, 1, k, 1),
+                  x2 = bnd_value(a, e, 0, 2, k, 1);
+                if (KAHAN) {
+                    kahan_add(q0, c0, al * (x0 - q0));
+                    kahan_add(q1, c1, al * (x1 - q1));
+                    kahan_add(q2, c2, al * (x2 - q2));
+                } else {
+                    q0 += al * (x0 - q0); q1 += al * (x1 - q1); q2 += al * (x2 - q2);
+                }
+            }
+            a.qout[0][s] = q0; a.qout[1][s] = q1; a.qout[2][s] = q2;
+            if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
+            if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, j * a.nx + i);
+            speed = cell_speed(a, q0, q1, q2, C.Hbar);
+        }
+    }
+    if (STAGE == 2) {
+        speed = block_max(speed, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) speed_atomic_max(a.ctl, speed);
+    }
+}
+
+// Max CFL speed of the current state (used at creation and on set_clock).
+template <typename T>
+__global__ void __launch_bounds__(256) speed_kernel(StageArgs<T> a) {
+    __shared__ T sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    T speed = T(0);
+    if (i < a.nx && j < a.ny) {
+        const long long cp = a.cpitch;
+        const T *H = a.H + (long long)j * cp + i;
+        T c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];
+        const T L = T(kLand);
+        if (!((c00 == L) | (c10 == L) | (c01 == L) | (c11 == L))) {
+            const long long s = (long long)j * a.pitch + i;
+            speed = cell_speed(a, a.qin[0][s], a.qin[1][s], a.qin[2][s],
+                               T(0.25) * (c00 + c10 + c01 + c11));
+        }
+    }
+    speed = block_max(speed, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) speed_atomic_max(a.ctl, speed);
+}
+
+// ---------------------------------------------------------------------------
+// the clock: t, dt, forcing brackets (FP64), one thread per domain
+
+__device__ void bracket(const double *times, int n, double t, int *k, double *s) {
+    if (n <= 1) { *k = 0; *s = 0.0; return; }
+    if (t <= times[0]) { *k = 0; *s = 0.0; return; }
+    if (t >= times[n - 1]) { *k = n - 2; *s = 1.0; return; }
+    int lo = 0, hi = n - 1;            // times[lo] <= t < times[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (times[mid] <= t) lo = mid; else hi = mid;
+    }
+    *k = lo;
+    *s = (t - times[lo]) / (times[lo + 1] - times[lo]);
+}
+
+__device__ void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
+                             const ForcingDev &wind, double speed, int mode) {
+    ctl->last_speed = speed;
+    if (mode == 1) { ctl->t += ctl->dt; ctl->step += 1; }
+    if (clk.dt_fixed > 0.0) {
+        ctl->dt = clk.dt_fixed;
+    } else if (mode == 0 || (mode == 1 && ctl->step % clk.dt_every == 0)) {
+        if (speed > 0.0 && isfinite(speed)) {
+            ctl->dt = clk.courant * 0.25 / speed;
+        } else if (ctl->err == ERR_NONE) {
+            ctl->err = ERR_NUMERIC;
+            ctl->err_step = ctl->step;
+        }
+    }
+    for (int s = 0; s < 2; s++) {
+        double tt = ctl->t + (s ? ctl->dt : 0.0);
+        bracket(bnd.times, bnd.n, tt, &ctl->bk[s], &ctl->bs[s]);
+        bracket(wind.times, wind.n, tt, &ctl->wk[s], &ctl->ws[s]);
+        ctl->tau[s][0] = ctl->tau[s][1] = 0.0;
+        if (wind.n > 0 && clk.wind_uniform) {
+            const float *A = wind.frames + 2LL * ctl->wk[s];
+            const float *B = wind.n > 1 ? A + 2 : A;
+            double w = ctl->ws[s];
+            double wx = (1.0 - w) * A[0] + w * B[0];
+            double wy = (1.0 - w) * A[1] + w * B[1];
+            double sp = sqrt(wx * wx + wy * wy);
+            double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
+            double k = clk.rho_ratio * cdrag * sp;
+            ctl->tau[s][0] = k * wx;
+            ctl->tau[s][1] = k * wy;
+        }
+    }
+}
+
+template <typename T>
+__global__ void clock_kernel(StepCtl *ctl, ClockParams clk, ForcingDev bnd, ForcingDev wind, int mode) {
+    double speed = sizeof(T) == 4 ? (double)__uint_as_float(ctl->speed32)
+                                  : __longlong_as_double((long long)ctl->speed64);
+    ctl->speed32 = 0u;
+    ctl->speed64 = 0ull;
+    clock_update(ctl, clk, bnd, wind, speed, mode);
+}
+
+__global__ void set_clock_kernel(StepCtl *ctl, double t, double dt, long long step) {
+    ctl->t = t;
+    ctl->step = step;
+    if (dt > 0.0) ctl->dt = dt;
+    ctl->speed32 = 0u;
+    ctl->speed64 = 0ull;
+    ctl->blocks_done = 0u;
+}
+
+__global__ void init_ctl_kernel(StepCtl *ctl, double t0) {
+    StepCtl z = {};
+    z.t = t0;
+    z.err_cell = -1;
+    *ctl = z;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: deterministic two-pass block sums
+
+template <typename T>
+__global__ void __launch_bounds__(256) diag_partial_kernel(StageArgs<T> a, double *partials) {
+    __shared__ double sh[2][8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double m = 0.0, en = 0.0;
+    if (i < a.nx && j < a.ny) {
+        const long long cp = a.cpitch;
+        const T *H = a.H + (long long)j * cp + i;
+        T c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];
+        const T L = T(kLand);
+        if (!((c00 == L) | (c10 == L) | (c01 == L) | (c11 == L))) {
+            const long long s = (long long)j * a.pitch + i;
+            double e = (double)a.qin[0][s], u = (double)a.qin[1][s], v = (double)a.qin[2][s];
+            double Hb = 0.25 * ((double)c00 + (double)c10 + (double)c01 + (double)c11);
+            double k = (double)a.kappa;
+            double h = e + Hb;
+            double mm = fmin(h * h / (2.0 * k) + 0.5 * k, k);
+            double hs = fmax(fabs(h), mm);
+            m = e;
+            en = 0.5 * (u * u + v * v) / hs + 0.5 * (double)a.g * e * e;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        en += __shfl_xor_sync(0xffffffffu, en, o);
+    }
+    int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if ((tid & 31) == 0) { sh[0][tid >> 5] = m; sh[1][tid >> 5] = en; }
+    __syncthreads();
+    if (tid == 0) {
+        double sm = 0.0, se = 0.0;
+        for (int w = 0; w < 8; w++) { sm += sh[0][w]; se += sh[1][w]; }
+        int b = blockIdx.y * gridDim.x + blockIdx.x;
+        partials[2 * b] = sm;
+        partials[2 * b + 1] = se;
+    }
+}
+
+__global__ void diag_final_kernel(const double *partials, int n, double area, double *out) {
+    __shared__ double sh[2][32];
+    double m = 0.0, e = 0.0;
+    // fixed assignment of partials to lanes, fixed combination order
+    for (int b = threadIdx.x; b < n; b += 32) { m += partials[2 * b]; e += partials[2 * b + 1]; }
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = e;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        double sm = 0.0, se = 0.0;
+        for (int w = 0; w < 32; w++) { sm += sh[0][w]; se += sh[1][w]; }
+        out[0] = sm * area;
+        out[1] = se * area;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+static dim3 ref_block() { return dim3(32, 8); }
+static dim3 ref_grid(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8); }
+
+template <typename T>
+cudaError_t launch_step_ref(const StageArgs<T> &a, cudaStream_t st, bool kahan) {
+    dim3 b = ref_block(), g = ref_grid(a.nx, a.ny);
+    stage_ref_kernel<T, 1, false><<<g, b, 0, st>>>(a);
+    if (kahan) stage_ref_kernel<T, 2, true><<<g, b, 0, st>>>(a);
+    else stage_ref_kernel<T, 2, false><<<g, b, 0, st>>>(a);
+    clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init_clock(const StageArgs<T> &a, cudaStream_t st, double t, double dt,
+                              long long step) {
+    set_clock_kernel<<<1, 1, 0, st>>>(a.ctl, t, dt, step);
+    if (dt > 0.0) {
+        clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 2);
+    } else {
+        speed_kernel<T><<<ref_grid(a.nx, a.ny), ref_block(), 0, st>>>(a);
+        clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 0);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_refresh_brackets(const StageArgs<T> &a, cudaStream_t st) {
+    clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctl_init(StepCtl *ctl, double t0, cudaStream_t st) {
+    init_ctl_kernel<<<1, 1, 0, st>>>(ctl, t0);
+    return cudaGetLastError();
+}
+
+int diag_blocks(int nx, int ny) {
+    dim3 g = ref_grid(nx, ny);
+    return (int)(g.x * g.y);
+}
+
+template <typename T>
+cudaError_t launch_diagnostics(const StageArgs<T> &a, double *partials, double *out,
+                               cudaStream_t st) {
+    dim3 g = ref_grid(a.nx, a.ny);
+    diag_partial_kernel<T><<<g, ref_block(), 0, st>>>(a, partials);
+    diag_final_kernel<<<1, 32, 0, st>>>(partials, (int)(g.x * g.y), (double)a.dx * (double)a.dy, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step_ref<float>(const StageArgs<float> &, cudaStream_t, bool);
+template cudaError_t launch_step_ref<double>(const StageArgs<double> &, cudaStream_t, bool);
+template cudaError_t launch_init_clock<float>(const StageArgs<float> &, cudaStream_t, double, double, long long);
+template cudaError_t launch_init_clock<double>(const StageArgs<double> &, cudaStream_t, double, double, long long);
+template cudaError_t launch_refresh_brackets<float>(const StageArgs<float> &, cudaStream_t);
+template cudaError_t launch_refresh_brackets<double>(const StageArgs<double> &, cudaStream_t);
+template cudaError_t launch_diagnostics<float>(const StageArgs<float> &, double *, double *, cudaStream_t);
+template cudaError_t launch_diagnostics<double>(const StageArgs<double> &, double *, double *, cudaStream_t);
+
+}  // namespace swe

@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 on the GPU within 1e-11 relative of the oracle; FP32 (plain
+and Kahan-compensated) within max |d eta| <= 1e-4 m and a relative L2 error
+of hu and hv <= 1e-4 after 1000 steps. Both sides compute their own adaptive
+time step from the same seeded float inputs."""
+import numpy as np
+import pytest
+
+from paper_1912_02457_gb300 import synth
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def swe():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1912_02457_gb300 import build, swe as S
+    build.build()
+    S.load()
+    return S
+
+
+def gpu_run(S, wl, n, precision, check=True):
+    with S.Domain(wl, precision) as d:
+        d.step(n)
+        info = d.info(check=check)
+        st = d.state()
+    return st, info
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_f32_parity(gpu, ref):
+    e, u, v = gpu
+    re, ru, rv = ref[:3]
+    assert np.abs(e.astype(np.float64) - re).max() <= 1e-4
+    assert rel_l2(u, ru) <= 1e-4
+    assert rel_l2(v, rv) <= 1e-4
+
+
+def test_gaussian_f64_1000_steps(swe, oracle_mod):
+    wl = synth.gaussian_bump(np.float64)
+    ref = oracle_mod.Oracle(wl).run(1000)
+    st, info = gpu_run(swe, wl, 1000, "f64")
+    for a, b in zip(st, ref[:3]):
+        assert helpers.rel(a, b) <= 1e-11
+    assert abs(info.t - ref[3]) <= 1e-11 * ref[3]
+    assert info.step == 1000
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_gaussian_f32_1000_steps(swe, oracle_mod, prec):
+    wl = synth.gaussian_bump(np.float32)
+    ref = oracle_mod.Oracle(wl).run(1000)
+    st, info = gpu_run(swe, wl, 1000, prec)
+    assert_f32_parity(st, ref)
+    assert abs(info.t - ref[3]) <= 1e-5 * ref[3]
+
+
+def _small_coastal(nx=96, ny=80, dtype=np.float64, member=0):
+    wl = synth.coastal(nx, ny, seed_config=92, member=member, dtype=dtype)
+    return wl
+
+
+def test_small_coastal_f64(swe, oracle_mod):
+    """Land, wet-dry shelves, nesting with tide frames at half resolution,
+    wind, drag, varying f and north angle: FP64 GPU vs oracle."""
+    wl = _small_coastal()
+    ref = oracle_mod.Oracle(wl).run(300)
+    st, info = gpu_run(swe, wl, 300, "f64")
+    for a, b in zip(st, ref[:3]):
+        assert helpers.rel(a, b) <= 1e-11
+    assert abs(info.t - ref[3]) <= 1e-11 * ref[3]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_small_coastal_f32(swe, oracle_mod, prec):
+    wl = _small_coastal(dtype=np.float32, member=1)
+    ref = oracle_mod.Oracle(wl).run(1000)
+    st, info = gpu_run(swe, wl, 1000, prec)
+    assert_f32_parity(st, ref)
+
+
+@pytest.mark.parametrize("shape", [(37, 23), (33, 9), (1, 17), (17, 1), (2, 2), (65, 130)])
+def test_ragged_shapes_f64(swe, oracle_mod, shape):
+    nx, ny = shape
+    wl = helpers.flat(nx, ny, depth=30.0, dx=500.0, dy=700.0, f=1e-4, theta=0.2)
+    wl.eta, wl.hu, wl.hv = helpers.random_state(wl, seed=nx * 131 + ny, amp=0.2, mom=1.0)
+    ref = oracle_mod.Oracle(wl).run(25)
+    st, info = gpu_run(swe, wl, 25, "f64")
+    for a, b in zip(st, ref[:3]):
+        assert helpers.rel(a, b) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan", "f64"])
+def test_lake_at_rest_bitwise(swe, prec):
+    dtype = np.float64 if prec == "f64" else np.float32
+    wl = helpers.rough(70, 50, seed=3, land=True, min_depth=0.5, cd=0.0025, dtype=dtype)
+    st, info = gpu_run(swe, wl, 50, prec)
+    for a, b in zip(st, (wl.eta, wl.hu, wl.hv)):
+        assert np.array_equal(a, b)
+
+
+def test_mass_conservation_f64(swe):
+    wl = synth.coastal(96, 64, seed_config=91, dtype=np.float64)
+    wl.bc = (synth.BC_WALL,) * 4
+    wl.boundary = None
+    with swe.Domain(wl, "f64") as d:
+        m0, _ = d.diagnostics()
+        d.step(200)
+        m1, _ = d.diagnostics()
+        e = d.read(swe.ETA)
+    scale = np.abs(e).sum() * wl.dx * wl.dy
+    assert abs(m1 - m0) < 1e-12 * scale
+
+
+def test_diagnostics_match_oracle(swe, oracle_mod):
+    wl = _small_coastal(dtype=np.float64, member=2)
+    with swe.Domain(wl, "f64") as d:
+        d.step(20)
+        st = d.state()
+        m, en = d.diagnostics()
+    om, oen = oracle_mod.Oracle(wl).diagnostics(*st)
+    assert abs(m - om) <= 1e-12 * max(abs(om), 1.0)
+    assert abs(en - oen) <= 1e-12 * abs(oen)
+
+
+@pytest.mark.parametrize("prec", ["f32_kahan", "f64"])
+def test_checkpoint_resume_bitwise(swe, prec):
+    dtype = np.float64 if prec == "f64" else np.float32
+    wl = _small_coastal(dtype=dtype, member=3)
+    with swe.Domain(wl, prec) as d:
+        d.step(60)
+        full = d.state()
+    with swe.Domain(wl, prec) as d:
+        d.step(25)
+        info = d.info()
+        ck = d.state()
+        comp = [d.read(k) for k in (swe.COMP_ETA, swe.COMP_HU, swe.COMP_HV)] if prec == "f32_kahan" else None
+    with swe.Domain(wl, prec) as d:
+        for k, a in zip((swe.ETA, swe.HU, swe.HV), ck):
+            d.write(k, a)
+        if comp is not None:
+            for k, a in zip((swe.COMP_ETA, swe.COMP_HU, swe.COMP_HV), comp):
+                d.write(k, a)
+        d.set_clock(info.t, info.dt, info.step)
+        d.step(35)
+        res = d.state()
+    for a, b in zip(full, res):
+        assert np.array_equal(a, b)
+
+
+def test_nonfinite_state_is_reported(swe):
+    wl = helpers.flat(40, 30, depth=20.0, dtype=np.float32)
+    with swe.Domain(wl, "f32") as d:
+        e = np.zeros((30, 40), np.float32)
+        e[7, 11] = np.nan
+        d.write(swe.ETA, e)
+        d.step(1)
+        info = d.info(check=False)
+        assert info.error == swe.ERR_NUMERIC
+        # the first cell found non-finite lies within the stencil's reach
+        cj, ci = divmod(info.error_cell, 40)
+        assert abs(ci - 11) + abs(cj - 7) <= 4
+        assert not np.isfinite(d.read(swe.ETA)[cj, ci])
+        with pytest.raises(swe.SweError):
+            d.info()
+        with pytest.raises(swe.SweError):
+            d.step(1)
+
+
+def test_all_land_has_no_time_step(swe):
+    wl = helpers.flat(8, 8, depth=20.0, dtype=np.float32)
+    wl.H[:] = synth.LAND
+    with swe.Domain(wl, "f32") as d:
+        assert d.info(check=False).error == swe.ERR_NUMERIC
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_coastal_1024_f32_1000_steps(swe, oracle_mod, prec):
+    """The full-size synthetic coastal domain (1024^2, ~30% land) through the
+    same entry point the benchmark times, 1000 steps against the oracle."""
+    wl = synth.coastal(1024, 1024, dtype=np.float32)
+    ref = _cached_coastal_reference(oracle_mod, wl)
+    st, info = gpu_run(swe, wl, 1000, prec)
+    assert_f32_parity(st, ref)
+
+
+_REF_CACHE = {}
+
+
+def _cached_coastal_reference(oracle_mod, wl):
+    if "c2" not in _REF_CACHE:
+        _REF_CACHE["c2"] = oracle_mod.Oracle(wl).run(1000)
+    return _REF_CACHE["c2"]

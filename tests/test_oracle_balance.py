@@ -164,3 +164,17 @@ def test_wall_equals_land_ring(oracle_mod):
     b = oracle_mod.Oracle(ring).run(12, dt_fixed=5.0)
     for x, y in zip(a[:3], b[:3]):
         assert helpers.rel(x, y[2:-2, 2:-2]) < 1e-13
+
+
+def test_wall_equals_land_ring_one_cell_wide(oracle_mod):
+    """A domain one cell wide (x or y) with walls: the second ghost row is
+    the double reflection of the single cell, which must again equal the same
+    column standing inside a ring of land."""
+    for nx, ny in ((1, 17), (17, 1)):
+        wl = helpers.flat(nx, ny, depth=30.0, dx=500.0, dy=700.0, f=1e-4, theta=0.2)
+        wl.eta, wl.hu, wl.hv = helpers.random_state(wl, seed=nx * 131 + ny, amp=0.2, mom=1.0)
+        ring = helpers.land_ring(wl, 2)
+        a = oracle_mod.Oracle(wl).run(25, dt_fixed=2.0)
+        b = oracle_mod.Oracle(ring).run(25, dt_fixed=2.0)
+        for x, y in zip(a[:3], b[:3]):
+            assert helpers.rel(x, y[2:-2, 2:-2]) < 1e-13
