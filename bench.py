@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the rotating shallow-water step on GB300.
+
+A "step" is one full SSP-RK2 time step of the scheme (both stages with
+their reconstruction, fluxes, sources and update, the flow relaxation of the
+nested edges, and the CFL reduction that sets the next time step) over the
+synthetic coastal domain: 1024 x 1024 cells at 800 m, ~30% land, wet-dry
+shelves, M2 tide on three nested edges from hourly frames, 10 m/s wind,
+quadratic drag, latitude 58-70 N, north angle 0-0.3 rad; FP32 arithmetic
+with Kahan-compensated state update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun each rank advances its own replica of
+the domain (no data-path collective); rank 0 reports the whole-job rate
+over the slowest rank's time. ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample, same metric).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and % HBM peak (single & batched); p50/p99 forecast latency"
+UNIT = "cell-updates/s"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_stage2_coastal1024.txt")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_config(nx, ny, precision):
+    return {
+        "workload": f"synthetic coastal {nx}x{ny} (800 m, ~30% land, wet-dry shelves, "
+                    "nested M2 tide frames, 10 m/s wind, Cd 0.0025, 58-70N, theta 0-0.3 rad)",
+        "nx": nx, "ny": ny, "precision": precision,
+        "step": "one SSP-RK2 step incl. flow relaxation and CFL reduction",
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "replicas (one domain per GPU)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# rank / timing helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, interval_ms: int = 20):
+        self.proc = None
+        self.lines = []
+        self.cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                    "-i", str(gpu_index), "-lms", str(interval_ms)]
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1912_02457_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv[f"dram_bytes_per_launch_{kernel}"])
+    except Exception:
+        return None
+
+
+def algorithmic_bytes(wl, precision):
+    """Bytes each launch must move ('Roofline'): a water cell
+    reads its state, its bathymetry corner and the f / theta planes and
+    writes its result; a land cell only needs its corner to know it is land.
+    Halo re-reads and forcing frames are not counted."""
+    n = wl.nx * wl.ny
+    land = int(wl.land_cells().sum())
+    wet = n - land
+    statics = 4 + (4 if wl.f is not None else 0) + (4 if wl.theta is not None else 0)
+    s1 = 12 + statics + 12                       # Q^n, statics -> D1
+    s2 = 12 + 12 + statics + 12                  # Q^n, D1, statics -> Q^{n+1}
+    if precision == "f32_kahan":
+        s2 += 24                                 # compensation read + write
+    return {"stage1": wet * s1 + land * 4, "stage2": wet * s2 + land * 4, "clock": 0,
+            "per_cell_step_wet": s1 + s2}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+
+def oracle_rate(steps: int, warmup: int, nside: int):
+    import oracle
+    from paper_1912_02457_gb300 import synth
+    wl = synth.coastal(nside, nside, dtype=np.float32)
+    o = oracle.Oracle(wl)
+    st = (wl.eta, wl.hu, wl.hv)
+    e, u, v, t, dt = o.run(max(warmup, 0)) if warmup > 0 else (*st, wl.t0, 0.0)
+    t0 = time.perf_counter()
+    o.run(steps, state=(e, u, v), t=t, dt=dt, step0=warmup)
+    el = time.perf_counter() - t0
+    return nside * nside * steps / el, el, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    nside = 256 if args.steps + args.warmup <= 5000 else 128
+    value, el, cores = oracle_rate(args.steps, args.warmup, nside)
+    sample = (f"oracle (FP64 C, OpenMP) on the same coastal recipe at {nside}x{nside}, "
+              f"{args.steps} timed steps after {args.warmup} warm-up steps")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / max(args.steps, 1) * (1024 * 1024) / (nside * nside),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(1024, 1024, args.precision),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args):
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    swe.load()
+
+    wl = synth.coastal(1024, 1024, dtype=np.float32)
+    cells = wl.nx * wl.ny
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dom = swe.Domain(wl, args.precision, stream=stream.cuda_stream)
+    parts = dom.launch_names()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        dom.step_profiled(1)
+    dom.info()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = np.zeros((args.steps, len(parts)))
+    launches0 = dom.info().launches
+    barrier()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[k][0].record(stream)
+            kernel_ms[k] = dom.step_profiled(1)[0]
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier()
+    info = dom.info()
+    launches = info.launches - launches0
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    device_s = float(step_ms.sum()) / 1e3
+    if ws > 1:
+        t = torch.tensor([device_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        device_s = float(t.item())
+    value = cells * args.steps * ws / device_s
+
+    # back-to-back steps without flushing (how a forecast actually runs)
+    torch.cuda.synchronize()
+    b2b_n = min(args.steps, 500)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    dom.step(b2b_n)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    b2b_ms = s0.elapsed_time(s1) / b2b_n
+
+    # end to end through the public API with pinned host buffers:
+    # upload the initial state, run the steps, download the final state
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (wl.eta, wl.hu, wl.hv)]
+    host_out = [torch.empty((wl.ny, wl.nx), dtype=torch.float32).pin_memory() for _ in range(3)]
+    fields = (swe.ETA, swe.HU, swe.HV)
+    torch.cuda.synchronize()
+    e2e_t0 = time.perf_counter()
+    for f, hbuf in zip(fields, host_in):
+        swe._check(dom._L.swe_write_state(dom.h, f, hbuf.data_ptr(), 0), "swe_write_state")
+    dom.set_clock(wl.t0, 0.0, 0)
+    dom.step(args.steps)
+    for f, hbuf in zip(fields, host_out):
+        swe._check(dom._L.swe_read_state(dom.h, f, hbuf.data_ptr(), 0), "swe_read_state")
+    e2e_s = time.perf_counter() - e2e_t0
+    e2e_info = dom.info()
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    bytes_state = 3 * cells * 4
+
+    # roofline of the dominant kernel
+    kern_avg = kernel_ms.mean(axis=0)
+    kern_tot = kernel_ms.sum(axis=0)
+    dom_k = int(np.argmax(kern_tot))
+    name = parts[dom_k]
+    ab = algorithmic_bytes(wl, args.precision)
+    peak, peak_src = measured_hbm_peak()
+    achieved = ab.get(name, 0) / (kern_avg[dom_k] * 1e-3) / 1e9
+    traffic = committed_traffic(name)
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            # the oracle on a bounded sample of the same workload (~10-30 s)
+            import oracle
+            o = oracle.Oracle(wl)
+            n_cpu = args.cpu_steps
+            c0 = time.perf_counter()
+            o.run(n_cpu)
+            cel = time.perf_counter() - c0
+            cpu = {"value": cells * n_cpu / cel, "unit": UNIT, "cores": oracle.num_threads(),
+                   "kind": "oracle",
+                   "sample": f"FP64 oracle, first {n_cpu} steps of the same 1024x1024 workload "
+                             f"({cel:.1f} s)"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * device_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": workload_config(wl.nx, wl.ny, args.precision),
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": ab.get(name, 0),
+                         "avg_launch_ms": float(kern_avg[dom_k])},
+            "kernels": {p: {"avg_ms": float(kern_avg[i]), "share": float(kern_tot[i] / kern_tot.sum())}
+                        for i, p in enumerate(parts)},
+            "back_to_back_ms_per_step": b2b_ms,
+            "back_to_back_value": cells / (b2b_ms * 1e-3),
+            "cpu_baseline": cpu,
+            "e2e": {"value": cells * args.steps * ws / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": bytes_state / args.steps,
+                    "d2h_bytes_per_step": bytes_state / args.steps,
+                    "job": f"upload state from pinned host, {args.steps} steps, download state"},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "wall_s_timed_region": wall,
+            "sim_time_s": info.t, "dt_s": info.dt,
+        }
+        if e2e_info.step != args.steps:
+            result["e2e"]["warning"] = "step count mismatch"
+        print(json.dumps(result), flush=True)
+    dom.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("f32", "f32_kahan"), default="f32_kahan")
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

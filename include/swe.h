@@ -69,6 +69,9 @@ typedef struct {
     double rho_air;         /* 1.225 (Section 3.5) */
     double rho_water;       /* 1025 */
     double t0;              /* initial simulated time, s */
+    int kernel;             /* 0: fastest kernels for the precision (FP32:
+                               sliding-window stage kernels); 1: the
+                               one-thread-per-cell reference kernels */
 } swe_params;
 
 /* Domain description. Arrays are read once by swe_create_domain and
@@ -96,6 +99,7 @@ typedef struct {
     int error_cell;         /* first offending cell (j*nx+i), -1 if none */
     long long error_step;   /* step at which it was found */
     double max_speed;       /* last CFL reduction: max (|u|+c)/dx, (|v|+c)/dy */
+    long long launches;     /* kernel launches issued by swe_step* so far */
 } swe_info;
 
 typedef struct swe_domain *swe_handle;
@@ -109,7 +113,7 @@ int swe_set_allocator(swe_alloc_fn alloc, swe_free_fn release, void *ctx);
 
 /* Defaults of the readings the paper leaves open: g = 9.81, theta = 1.3,
  * kappa = 1e-2 m, C_d = 0, Courant 0.8 (Section 5), d0 = 2.5, zone 10
- * cells, dt every step, rho_air 1.225, rho_water 1025, t0 = 0. */
+ * cells, dt every step, rho_air 1.225, rho_water 1025, t0 = 0, kernel 0. */
 void swe_default_params(swe_params *p);
 
 /* Create a domain: validate the description, allocate its device planes,
@@ -149,6 +153,17 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times,
  * Errors: SWE_ERR_INVALID_ARG, SWE_ERR_CUDA (launch), SWE_ERR_NUMERIC
  * (a sticky device error was already observed). */
 int swe_step(swe_handle h, int n_steps);
+
+/* Kernel launches one step issues, and the name of launch `part` of a step
+ * ("stage1", "stage2", ...). For measurement tools. */
+int swe_launches_per_step(swe_handle h);
+const char *swe_launch_name(swe_handle h, int part);
+
+/* swe_step with a CUDA event recorded before and after every kernel
+ * launch; synchronises at the end and writes each launch's device time in
+ * ms to ms[0 .. n_steps * swe_launches_per_step(h) - 1], in launch order.
+ * capacity: elements of ms. Same numerics as swe_step. */
+int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity);
 
 /* Copy one field of the current state (nx*ny, row-major, element type of
  * the domain's precision) to dst, host or device memory. Stream-ordered;

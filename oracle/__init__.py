@@ -50,6 +50,7 @@ class _Domain(C.Structure):
         ("wind_t", C.POINTER(C.c_double)), ("wind", C.POINTER(C.c_double)),
         ("bnd_n", C.c_int), ("bnd_nbx", C.c_int), ("bnd_nby", C.c_int),
         ("bnd_t", C.POINTER(C.c_double)), ("bnd", C.POINTER(C.c_double)),
+        ("round_state_f32", C.c_int),
     ]
 
 
@@ -102,7 +103,7 @@ def _p(a):
 class Oracle:
     """The oracle bound to one workload's statics and forcing."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, round_state_f32: bool = False):
         self.wl = wl
         p = wl.params
         nx, ny = wl.nx, wl.ny
@@ -132,6 +133,7 @@ class Oracle:
             bt, bv = keep(wl.boundary.times), keep(wl.boundary.frames)
             D.bnd_n, D.bnd_nbx, D.bnd_nby = len(bt), wl.boundary.nfx, wl.boundary.nfy
             D.bnd_t, D.bnd = _p(bt), _p(bv)
+        D.round_state_f32 = int(bool(round_state_f32))
         self.D = D
         self.L = lib()
 

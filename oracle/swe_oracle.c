@@ -61,6 +61,10 @@ typedef struct {
     /* nesting frames: bnd_n frames of 12*(nbx+nby) at bnd_t */
     int bnd_n, bnd_nbx, bnd_nby;
     const double *bnd_t, *bnd;
+    /* 1: round the stored state to float32 after every stage (the storage
+     * precision of the paper's GPU code, Section 3.2); arithmetic stays FP64.
+     * Used to measure how sensitive a solution is to float32 storage. */
+    int round_state_f32;
 } orc_domain;
 
 /* ------------------------------------------------------------------------ */
@@ -781,6 +785,8 @@ static void step(const orc_domain *d, const statics *S, work *W,
         qs[np + s] = (hu[s] + dt * M[np + s]) / (1.0 + dt * Sf[s]);
         qs[2 * np + s] = (hv[s] + dt * M[2 * np + s]) / (1.0 + dt * Sf[s]);
     }
+    if (d->round_state_f32)
+        for (size_t s = 0; s < 3 * np; s++) qs[s] = (double)(float)qs[s];
     rhs(d, S, W, qs, qs + np, qs + 2 * np, t + dt, M, Sf);
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -791,6 +797,12 @@ static void step(const orc_domain *d, const statics *S, work *W,
             hv[s] = 0.5 * (hv[s] + qs[2 * np + s] + dt * M[2 * np + s]) / (1.0 + 0.5 * dt * Sf[s]);
         }
     apply_frs(d, eta, hu, hv, t + dt);
+    if (d->round_state_f32)
+        for (size_t s = 0; s < np; s++) {
+            eta[s] = (double)(float)eta[s];
+            hu[s] = (double)(float)hu[s];
+            hv[s] = (double)(float)hv[s];
+        }
 }
 
 int orc_step(const orc_domain *d, double *eta, double *hu, double *hv,

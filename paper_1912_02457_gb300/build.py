@@ -21,6 +21,9 @@ LIB = os.path.join(OUT_DIR, "libswe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# per-file flags: the FP32 fast path uses the approximate reciprocal and
+# square root (about 1 ulp); the reference kernels stay IEEE
+FILE_FLAGS = {"swe_stage_fast.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc():
@@ -57,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []),
+               *extra_flags, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

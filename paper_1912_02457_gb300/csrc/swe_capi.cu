@@ -63,6 +63,11 @@ struct swe_domain {
     double *diag_partials = nullptr;
     double *diag_out = nullptr;
     bool sticky_numeric = false;
+    long long launches = 0;
+    std::vector<cudaEvent_t> events;   // profiling pool, grown on demand
+
+    bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
+    int parts() const { return fast() ? swe::fast_step_parts() : swe::ref_step_parts(); }
 
     void *dalloc(size_t bytes) {
         void *ptr = nullptr;
@@ -82,6 +87,8 @@ struct swe_domain {
         else cudaFree(ptr);
     }
     void free_all() {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        events.clear();
         for (void *ptr : owned) {
             if (release) release(ptr, stream, alloc_ctx);
             else cudaFree(ptr);
@@ -234,6 +241,7 @@ int validate(const swe_domain_desc *d, const swe_params *p) {
     if (!(p->g > 0) || !(p->kappa > 0) || !(p->courant > 0) || !(p->frs_d0 > 0)) return SWE_ERR_INVALID_ARG;
     if (p->cd < 0 || p->theta_mm < 1.0 || p->theta_mm > 2.0) return SWE_ERR_INVALID_ARG;
     if (p->dt_fixed < 0 || !(p->rho_water > 0) || p->rho_air < 0) return SWE_ERR_INVALID_ARG;
+    if (p->kernel != 0 && p->kernel != 1) return SWE_ERR_INVALID_ARG;
     return SWE_OK;
 }
 
@@ -285,6 +293,7 @@ void swe_default_params(swe_params *p) {
     p->rho_air = 1.225;
     p->rho_water = 1025.0;
     p->t0 = 0.0;
+    p->kernel = 0;
 }
 
 int swe_create_domain(const swe_domain_desc *d, const swe_params *p, void *stream, swe_handle *out) {
@@ -337,19 +346,73 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times, c
     return SWE_OK;
 }
 
-int swe_step(swe_handle h, int n_steps) {
+namespace {
+
+int step_check(swe_handle h, int n_steps) {
     if (!h || n_steps < 0) return SWE_ERR_INVALID_ARG;
     if (h->sticky_numeric) return SWE_ERR_NUMERIC;
     if ((h->bc[0] == SWE_BC_NESTED || h->bc[1] == SWE_BC_NESTED || h->bc[2] == SWE_BC_NESTED ||
          h->bc[3] == SWE_BC_NESTED) && h->bnd_n == 0)
         return SWE_ERR_INVALID_ARG;
+    return SWE_OK;
+}
+
+int launch_part(swe_handle h, int part) {
+    cudaError_t e;
+    if (h->prec == SWE_F64) e = swe::launch_step_ref_part(make_args<double>(h), h->stream, part, false);
+    else if (h->fast()) e = swe::launch_step_fast_part(make_args<float>(h), h->stream, part, h->prec == SWE_F32_KAHAN);
+    else e = swe::launch_step_ref_part(make_args<float>(h), h->stream, part, h->prec == SWE_F32_KAHAN);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->launches++;
+    return SWE_OK;
+}
+
+}  // namespace
+
+int swe_step(swe_handle h, int n_steps) {
+    int rc = step_check(h, n_steps);
+    if (rc) return rc;
+    const int parts = h->parts();
     for (int s = 0; s < n_steps; s++) {
-        cudaError_t e;
-        if (h->prec == SWE_F64) e = swe::launch_step_ref(make_args<double>(h), h->stream, false);
-        else e = swe::launch_step_ref(make_args<float>(h), h->stream, h->prec == SWE_F32_KAHAN);
-        if (e != cudaSuccess) return cuda_fail(e);
+        for (int p = 0; p < parts; p++)
+            if ((rc = launch_part(h, p))) return rc;
         h->cur ^= 1;
     }
+    return SWE_OK;
+}
+
+int swe_launches_per_step(swe_handle h) {
+    if (!h) return SWE_ERR_INVALID_ARG;
+    return h->parts();
+}
+
+const char *swe_launch_name(swe_handle h, int part) {
+    if (!h) return "";
+    return h->fast() ? swe::fast_part_name(part) : swe::ref_part_name(part);
+}
+
+int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
+    int rc = step_check(h, n_steps);
+    if (rc) return rc;
+    const int parts = h->parts();
+    if (!ms || capacity < n_steps * parts) return SWE_ERR_INVALID_ARG;
+    const size_t need = (size_t)2 * n_steps * parts;
+    while (h->events.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->events.push_back(e);
+    }
+    size_t k = 0;
+    for (int s = 0; s < n_steps; s++) {
+        for (int p = 0; p < parts; p++) {
+            CK(cudaEventRecord(h->events[k++], h->stream));
+            if ((rc = launch_part(h, p))) return rc;
+            CK(cudaEventRecord(h->events[k++], h->stream));
+        }
+        h->cur ^= 1;
+    }
+    CK(cudaEventSynchronize(h->events[need - 1]));
+    for (size_t q = 0; q < need / 2; q++) CK(cudaEventElapsedTime(&ms[q], h->events[2 * q], h->events[2 * q + 1]));
     return SWE_OK;
 }
 
@@ -400,6 +463,7 @@ int swe_get_info(swe_handle h, swe_info *out) {
     out->error_cell = c.err_cell;
     out->error_step = c.err_step;
     out->max_speed = c.last_speed;
+    out->launches = h->launches;
     if (c.err != 0) {
         h->sticky_numeric = true;
         return SWE_ERR_NUMERIC;

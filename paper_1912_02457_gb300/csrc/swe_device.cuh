@@ -230,4 +230,117 @@ __device__ T bnd_value(const StageArgs<T> &a, int e, int r, int v, int k, int st
     return T((1.0 - s) * va + s * vb);
 }
 
+
+__device__ __forceinline__ void axis_pos_f(int k, int n, int nb, int &k0, int &k1, float &w) {
+    float p = (k + 0.5f) * (float)nb / (float)n - 0.5f;
+    p = fminf(fmaxf(p, 0.0f), (float)(nb - 1));
+    int q = (int)floorf(p);
+    if (q > nb - 1) q = nb - 1;
+    k0 = q;
+    k1 = q + 1 < nb ? q + 1 : nb - 1;
+    w = p - q;
+}
+
+// Wind stress at cell (i, j) at the stage time (Section 3.5): uniform
+// frames use the stress the clock kernel computed in FP64; gridded frames
+// are sampled bilinearly at the cell centre and lerped in time here.
+template <typename T>
+__device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int stage,
+                                        T rho_ratio, T &tx, T &ty) {
+    if (a.wind.n <= 0) { tx = T(0); ty = T(0); return; }
+    if (a.clk.wind_uniform) {
+        tx = T(a.ctl->tau[stage][0]);
+        ty = T(a.ctl->tau[stage][1]);
+        return;
+    }
+    const ForcingDev &F = a.wind;
+    int x0, x1, y0, y1;
+    float wx, wy;
+    axis_pos_f(i, a.nx, F.n1, x0, x1, wx);
+    axis_pos_f(j, a.ny, F.n2, y0, y1, wy);
+    int fk = a.ctl->wk[stage];
+    float s = (float)a.ctl->ws[stage];
+    long long fs = 2LL * F.n1 * F.n2;
+    const float *A = F.frames + fk * fs;
+    const float *B = F.n > 1 ? A + fs : A;
+    float W[2];
+    for (int c = 0; c < 2; c++) {
+        float a0 = (1.f - wx) * A[(y0 * F.n1 + x0) * 2 + c] + wx * A[(y0 * F.n1 + x1) * 2 + c];
+        float a1 = (1.f - wx) * A[(y1 * F.n1 + x0) * 2 + c] + wx * A[(y1 * F.n1 + x1) * 2 + c];
+        float b0 = (1.f - wx) * B[(y0 * F.n1 + x0) * 2 + c] + wx * B[(y0 * F.n1 + x1) * 2 + c];
+        float b1 = (1.f - wx) * B[(y1 * F.n1 + x0) * 2 + c] + wx * B[(y1 * F.n1 + x1) * 2 + c];
+        W[c] = (1.f - s) * ((1.f - wy) * a0 + wy * a1) + s * ((1.f - wy) * b0 + wy * b1);
+    }
+    wind_stress<T>(T(W[0]), T(W[1]), rho_ratio, tx, ty);
+}
+
+// CFL wave speed of one cell, eq:cfl: max((|u| + sqrt(g hbar+))/dx,
+// (|v| + sqrt(g hbar+))/dy) with desingularised cell velocities.
+template <typename T>
+__device__ __forceinline__ T cell_speed(const StageArgs<T> &a, T eta, T hu, T hv, T Hbar) {
+    T hbar = eta + Hbar;
+    T hs = desing(hbar, a.kappa, a.half_inv_kappa);
+    T c = sqrt(a.g * fmax(hbar, T(0)));
+    T r = T(1) / hs;
+    T sx = (fabs(hu * r) + c) * a.inv_dx;
+    T sy = (fabs(hv * r) + c) * a.inv_dy;
+    return fmax(sx, sy);
+}
+
+__device__ inline void flag_error(StepCtl *ctl, int cell) {
+    if (atomicCAS(&ctl->err_cell, -1, cell) == -1) {
+        ctl->err = ERR_NUMERIC;
+        ctl->err_step = ctl->step;
+    }
+}
+
+// The clock: t, dt and forcing brackets in FP64 (one thread per domain).
+__device__ __forceinline__ void bracket(const double *times, int n, double t, int *k, double *s) {
+    if (n <= 1) { *k = 0; *s = 0.0; return; }
+    if (t <= times[0]) { *k = 0; *s = 0.0; return; }
+    if (t >= times[n - 1]) { *k = n - 2; *s = 1.0; return; }
+    int lo = 0, hi = n - 1;            // times[lo] <= t < times[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (times[mid] <= t) lo = mid; else hi = mid;
+    }
+    *k = lo;
+    *s = (t - times[lo]) / (times[lo + 1] - times[lo]);
+}
+
+__device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
+                             const ForcingDev &wind, double speed, int mode) {
+    ctl->last_speed = speed;
+    if (mode == 1) { ctl->t += ctl->dt; ctl->step += 1; }
+    if (clk.dt_fixed > 0.0) {
+        ctl->dt = clk.dt_fixed;
+    } else if (mode == 0 || (mode == 1 && ctl->step % clk.dt_every == 0)) {
+        if (speed > 0.0 && isfinite(speed)) {
+            ctl->dt = clk.courant * 0.25 / speed;
+        } else if (ctl->err == ERR_NONE) {
+            ctl->err = ERR_NUMERIC;
+            ctl->err_step = ctl->step;
+        }
+    }
+    for (int s = 0; s < 2; s++) {
+        double tt = ctl->t + (s ? ctl->dt : 0.0);
+        bracket(bnd.times, bnd.n, tt, &ctl->bk[s], &ctl->bs[s]);
+        bracket(wind.times, wind.n, tt, &ctl->wk[s], &ctl->ws[s]);
+        ctl->tau[s][0] = ctl->tau[s][1] = 0.0;
+        if (wind.n > 0 && clk.wind_uniform) {
+            const float *A = wind.frames + 2LL * ctl->wk[s];
+            const float *B = wind.n > 1 ? A + 2 : A;
+            double w = ctl->ws[s];
+            double wx = (1.0 - w) * A[0] + w * B[0];
+            double wy = (1.0 - w) * A[1] + w * B[1];
+            double sp = sqrt(wx * wx + wy * wy);
+            double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
+            double k = clk.rho_ratio * cdrag * sp;
+            ctl->tau[s][0] = k * wx;
+            ctl->tau[s][1] = k * wy;
+        }
+    }
+}
+
+
 }  // namespace swe

@@ -4,8 +4,10 @@
 
 namespace swe {
 
+int ref_step_parts();
+const char *ref_part_name(int part);
 template <typename T>
-cudaError_t launch_step_ref(const StageArgs<T> &a, cudaStream_t st, bool kahan);
+cudaError_t launch_step_ref_part(const StageArgs<T> &a, cudaStream_t st, int part, bool kahan);
 template <typename T>
 cudaError_t launch_init_clock(const StageArgs<T> &a, cudaStream_t st, double t, double dt,
                               long long step);
@@ -15,6 +17,12 @@ template <typename T>
 cudaError_t launch_diagnostics(const StageArgs<T> &a, double *partials, double *out,
                                cudaStream_t st);
 cudaError_t launch_ctl_init(StepCtl *ctl, double t0, cudaStream_t st);
+
+// FP32 sliding-window stage kernels (swe_stage_fast.cu): stage 1, then
+// stage 2 with the fused CFL reduction and clock update.
+int fast_step_parts();
+const char *fast_part_name(int part);
+cudaError_t launch_step_fast_part(const StageArgs<float> &a, cudaStream_t st, int part, bool kahan);
 int diag_blocks(int nx, int ny);
 
 }  // namespace swe

@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("cd", C.c_double), ("courant", C.c_double), ("frs_d0", C.c_double),
                 ("frs_width", C.c_int), ("dt_update_every", C.c_int),
                 ("dt_fixed", C.c_double), ("rho_air", C.c_double),
-                ("rho_water", C.c_double), ("t0", C.c_double)]
+                ("rho_water", C.c_double), ("t0", C.c_double), ("kernel", C.c_int)]
 
 
 class DomainDesc(C.Structure):
@@ -52,7 +52,7 @@ class DomainDesc(C.Structure):
 class Info(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("step", C.c_longlong),
                 ("error", C.c_int), ("error_cell", C.c_int), ("error_step", C.c_longlong),
-                ("max_speed", C.c_double)]
+                ("max_speed", C.c_double), ("launches", C.c_longlong)]
 
 
 _lib = None
@@ -72,6 +72,9 @@ SIGNATURES = {
     "swe_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                   C.c_int, C.c_int]),
     "swe_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "swe_launches_per_step": (C.c_int, [C.c_void_p]),
+    "swe_launch_name": (C.c_char_p, [C.c_void_p, C.c_int]),
+    "swe_step_profiled": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "swe_read_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "swe_write_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "swe_set_clock": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_longlong]),
@@ -116,12 +119,13 @@ def default_params() -> Params:
     return p
 
 
-def params_from(wl_params, t0=0.0) -> Params:
+def params_from(wl_params, t0=0.0, kernel=0) -> Params:
     p = default_params()
     for k in ("g", "theta_mm", "kappa", "cd", "courant", "frs_d0", "frs_width",
               "dt_update_every", "dt_fixed", "rho_air", "rho_water"):
         setattr(p, k, getattr(wl_params, k))
     p.t0 = t0
+    p.kernel = kernel
     return p
 
 
@@ -152,7 +156,7 @@ class Domain:
     'f32', 'f32_kahan', 'f64'; ``stream`` a cudaStream_t as an int (0: the
     legacy default stream, which is also PyTorch's default stream)."""
 
-    def __init__(self, wl, precision: str = "f32", stream: int = 0):
+    def __init__(self, wl, precision: str = "f32", stream: int = 0, kernel: str = "fast"):
         L = load()
         self.wl = wl
         self.prec = PRECISIONS[precision]
@@ -175,7 +179,7 @@ class Domain:
         d.theta = arr(wl.theta) if wl.theta is not None else None
         d.f_const, d.theta_const = wl.f_const, wl.theta_const
         d.src_is_device = 0
-        p = params_from(wl.params, wl.t0)
+        p = params_from(wl.params, wl.t0, {"fast": 0, "reference": 1}[kernel])
         h = C.c_void_p()
         _check(L.swe_create_domain(C.byref(d), C.byref(p), C.c_void_p(stream), C.byref(h)),
                "swe_create_domain")
@@ -194,6 +198,19 @@ class Domain:
 
     def step(self, n: int):
         _check(self._L.swe_step(self.h, int(n)), "swe_step")
+
+    def launches_per_step(self) -> int:
+        return self._L.swe_launches_per_step(self.h)
+
+    def launch_names(self):
+        return [self._L.swe_launch_name(self.h, k).decode() for k in range(self.launches_per_step())]
+
+    def step_profiled(self, n: int) -> np.ndarray:
+        """Step n times; return per-launch device times (ms), shape (n, parts)."""
+        parts = self.launches_per_step()
+        ms = np.zeros(n * parts, dtype=np.float32)
+        _check(self._L.swe_step_profiled(self.h, int(n), ms.ctypes.data, ms.size), "swe_step_profiled")
+        return ms.reshape(n, parts)
 
     def read(self, field: int) -> np.ndarray:
         out = np.empty((self.ny, self.nx), dtype=self.dtype)
