@@ -100,6 +100,8 @@ typedef struct {
     long long error_step;   /* step at which it was found */
     double max_speed;       /* last CFL reduction: max (|u|+c)/dx, (|v|+c)/dy */
     long long launches;     /* kernel launches issued by swe_step* so far */
+    int done;               /* 1 once t reached the end time: steps are no-ops */
+    double t_end;           /* end time set by swe_set_end_time, 0 if none */
 } swe_info;
 
 typedef struct swe_domain *swe_handle;
@@ -148,11 +150,18 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times,
  * eq:rk2_semiimp with the central-upwind fluxes eqn:numerical_flux,
  * asynchronously on the domain's stream. Each step: stage 1 at t, stage 2
  * at t + dt, flow relaxation, then the fused CFL reduction sets the next
- * dt on the device (no host synchronisation). Numerical failures are
- * reported through swe_get_info / the next synchronising call.
+ * dt on the device (no host synchronisation). Runs of 16 steps replay one
+ * CUDA graph (captured on first use, rebuilt after swe_set_forcing).
+ * Numerical failures are reported through swe_get_info / the next
+ * synchronising call.
  * Errors: SWE_ERR_INVALID_ARG, SWE_ERR_CUDA (launch), SWE_ERR_NUMERIC
  * (a sticky device error was already observed). */
 int swe_step(swe_handle h, int n_steps);
+
+/* Forecast horizon: the step that would pass t_end is shortened to end
+ * exactly at t_end, after which steps leave the state and clock unchanged
+ * (swe_info.done = 1). t_end = 0 removes the horizon. Stream-ordered. */
+int swe_set_end_time(swe_handle h, double t_end);
 
 /* Kernel launches one step issues, and the name of launch `part` of a step
  * ("stage1", "stage2", ...). For measurement tools. */
@@ -193,6 +202,48 @@ int swe_diagnostics(swe_handle h, double out[2]);
 
 /* Release every resource of the domain after its stream drains. */
 int swe_destroy_domain(swe_handle h);
+
+/* ---- batches: ensembles and served forecasts --------------------------
+ * A batch advances many FP32 domains (of any sizes, each with its own
+ * clock, dt, forcing and horizon) by ONE persistent launch per RK stage:
+ * every block walks a device-resident table of tiles covering all domains,
+ * and each domain's CFL reduction and clock update are done by its own last
+ * tile. Runs of 8 batch steps replay one CUDA graph; because the tables,
+ * parities, clocks and horizons live on the device, the graph stays valid
+ * when domains are added or removed. The result of every domain is bitwise
+ * the same as stepping it alone (the per-cell arithmetic does not depend on
+ * the tiling). While in a batch a domain must be stepped only through it;
+ * read its state after swe_batch_sync. A domain that reached its end time
+ * (swe_set_end_time) is skipped at no cost. */
+typedef struct swe_batch *swe_batch_handle;
+
+/* Create an empty batch working on `stream`, with table room for
+ * max_domains domains. Allocates device memory. */
+int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out);
+/* Add / remove a domain (FP32 or FP32_KAHAN with the fast kernels;
+ * SWE_ERR_UNSUPPORTED otherwise). Both drain the streams involved. */
+int swe_batch_add(swe_batch_handle b, swe_handle d);
+int swe_batch_remove(swe_batch_handle b, swe_handle d);
+int swe_batch_size(swe_batch_handle b);
+/* Tile height (rows per warp item; items are 28 columns wide, four to a
+ * block). 0 = autotune:
+ * the first swe_batch_step of >= 16 steps times 2 steps with each of the
+ * heights 8, 16, 32, 64 and keeps the fastest (these are real steps).
+ * swe_batch_rows returns the current choice (0 until tuned). */
+int swe_batch_set_rows(swe_batch_handle b, int rows);
+int swe_batch_rows(swe_batch_handle b);
+/* Advance every domain of the batch n_steps steps (asynchronous). */
+int swe_batch_step(swe_batch_handle b, int n_steps);
+/* The same steps launched the plain way, domain after domain, two kernels
+ * per domain per step (the baseline the batched path is measured against). */
+int swe_batch_step_serial(swe_batch_handle b, int n_steps);
+int swe_batch_sync(swe_batch_handle b);
+/* Synchronise, then report per domain (in add order) whether it reached
+ * its end time and its simulated time. capacity >= swe_batch_size. */
+int swe_batch_poll(swe_batch_handle b, int *done, double *t, int capacity);
+/* Kernel launches issued by this batch so far. */
+long long swe_batch_launches(swe_batch_handle b);
+int swe_batch_destroy(swe_batch_handle b);
 
 /* The last CUDA error string recorded by this thread, or "". */
 const char *swe_last_cuda_error(void);

@@ -81,7 +81,7 @@ def lib():
             L.orc_run.restype = C.c_int
             L.orc_run.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, _dp, _dp,
                                   C.c_long, C.c_int, C.c_double, C.c_double,
-                                  C.c_int, _dp]
+                                  C.c_int, _dp, C.c_double]
             L.orc_diagnostics.restype = None
             L.orc_diagnostics.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, _dp, _dp]
             L.orc_face_flux.restype = None
@@ -168,7 +168,7 @@ class Oracle:
 
     # -- time stepping -----------------------------------------------------
     def run(self, n_steps, state=None, t=None, dt=0.0, step0=0, dt_fixed=None,
-            courant=None, dt_every=None, return_dts=False):
+            courant=None, dt_every=None, return_dts=False, t_end=0.0):
         """Advance ``n_steps`` from ``state`` (default: the workload's initial
         state) and return (eta, hu, hv, t, dt[, dts])."""
         wl = self.wl
@@ -184,7 +184,7 @@ class Oracle:
                             p.courant if courant is None else courant,
                             p.dt_fixed if dt_fixed is None else dt_fixed,
                             p.dt_update_every if dt_every is None else dt_every,
-                            _p(dts))
+                            _p(dts), float(t_end))
         if rc:
             raise RuntimeError(f"oracle run failed (rc={rc})")
         out = (e, u, v, tt.value, dd.value)

@@ -858,14 +858,16 @@ double orc_cfl_dt(const orc_domain *d, const double *eta, const double *hu,
     return courant * 0.25 / orc_max_speed(d, eta, hu, hv);
 }
 
-/* Advance n steps from time *t. dt policy: a fixed dt when dt_fixed > 0,
+/* Advance n steps from time *t (steps past t_end > 0 are skipped, and the
+ * step that would pass it is shortened to end on it). dt policy: a fixed
+ * dt when dt_fixed > 0,
  * otherwise dt is recomputed from the current state before every step whose
  * global index (step0 + k) is a multiple of dt_every, and held in between
  * (Section 5 recomputes it every 20 simulated minutes). *dt carries the
  * held value in and out; dts (optional) receives each step's dt. */
 int orc_run(const orc_domain *d, double *eta, double *hu, double *hv,
             double *t, double *dt, long step0, int n, double courant,
-            double dt_fixed, int dt_every, double *dts)
+            double dt_fixed, int dt_every, double *dts, double t_end)
 {
     size_t np = (size_t)d->nx * d->ny;
     if (dt_every < 1) dt_every = 1;
@@ -881,6 +883,11 @@ int orc_run(const orc_domain *d, double *eta, double *hu, double *hv,
         if (dt_fixed > 0.0) *dt = dt_fixed;
         else if (s % dt_every == 0 || !(*dt > 0.0)) *dt = orc_cfl_dt(d, eta, hu, hv, courant);
         if (!(*dt > 0.0) || !isfinite(*dt)) { rc = -2; break; }
+        /* a forecast horizon: the step that would pass t_end ends on it */
+        if (t_end > 0.0) {
+            if (*t >= t_end * (1.0 - 1e-14)) { if (dts) dts[k] = 0.0; continue; }
+            if (*t + *dt > t_end) *dt = t_end - *t;
+        }
         step(d, &S, &W, eta, hu, hv, *t, *dt, M, Sf, qs);
         if (dts) dts[k] = *dt;
         *t += *dt;

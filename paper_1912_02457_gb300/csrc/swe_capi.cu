@@ -52,7 +52,6 @@ struct swe_domain {
     void *comp[3] = {nullptr};
     void *H = nullptr, *f = nullptr, *th = nullptr;
     double f_const = 0, th_const = 0;
-    int cur = 0;
     StepCtl *ctl = nullptr;
     float *bnd = nullptr;
     double *bnd_t = nullptr;
@@ -65,6 +64,23 @@ struct swe_domain {
     bool sticky_numeric = false;
     long long launches = 0;
     std::vector<cudaEvent_t> events;   // profiling pool, grown on demand
+
+    // graph of kGraphSteps steps, captured on a private stream and replayed
+    // on `stream`; every kernel reads the parity and clock from the device,
+    // so one graph serves every step until the forcing buffers change
+    static constexpr int kGraphSteps = 16;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+
+    void drop_graph() {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+
+    // one-entry tile table of the FP32 fast path (same kernel as batches)
+    swe::StageArgs<float> *t_args = nullptr;
+    int *t_start = nullptr, *t_gx = nullptr, *t_rows = nullptr, *t_n = nullptr;
+    int t_tiles = 0;
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
     int parts() const { return fast() ? swe::fast_step_parts() : swe::ref_step_parts(); }
@@ -87,6 +103,9 @@ struct swe_domain {
         else cudaFree(ptr);
     }
     void free_all() {
+        drop_graph();
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        capture_stream = nullptr;
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         events.clear();
         for (void *ptr : owned) {
@@ -126,16 +145,18 @@ StageArgs<T> make_args(const swe_domain *d) {
     a.f_const = T(d->f_const);
     a.th_const = T(d->th_const);
     for (int k = 0; k < 3; k++) {
-        a.qin[k] = (const T *)d->q[d->cur][k];
-        a.qout[k] = (T *)d->q[1 - d->cur][k];
+        a.q[0][k] = (T *)d->q[0][k];
+        a.q[1][k] = (T *)d->q[1][k];
         a.d1[k] = (T *)d->d1[k];
         a.comp[k] = (T *)d->comp[k];
     }
     a.bnd = swe::ForcingDev{d->bnd, d->bnd_t, d->bnd_n, d->bnd_n1, d->bnd_n2};
     a.wind = swe::ForcingDev{d->wind, d->wind_t, d->wind_n, d->wind_n1, d->wind_n2};
     a.frs_width = d->p.frs_width;
-    for (int k = 0; k < swe::kMaxFrs; k++)
+    for (int k = 0; k < swe::kMaxFrs; k++) {
         a.frs_alpha[k] = k < d->p.frs_width ? 1.0 - std::tanh((double)k / d->p.frs_d0) : 0.0;
+        a.frs_alpha_f[k] = (float)a.frs_alpha[k];
+    }
     a.ctl = d->ctl;
     a.clk.courant = d->p.courant;
     a.clk.dt_fixed = d->p.dt_fixed;
@@ -143,6 +164,32 @@ StageArgs<T> make_args(const swe_domain *d) {
     a.clk.wind_uniform = (d->wind_n1 == 1 && d->wind_n2 == 1) ? 1 : 0;
     a.clk.rho_ratio = d->p.rho_air / d->p.rho_water;
     return a;
+}
+
+// (Re)write the domain's own one-entry tile table (fast FP32 path).
+int upload_table(swe_domain *d) {
+    if (!d->fast()) return SWE_OK;
+    swe::StageArgs<float> a = make_args<float>(d);
+    int rows = swe::fast_rows(d->nx, d->ny), gx = 0;
+    d->t_tiles = swe::fast_tiles(d->nx, d->ny, rows, &gx);
+    int start[2] = {0, d->t_tiles}, one = 1;
+    CK(cudaStreamSynchronize(d->stream));
+    CK(cudaMemcpy(d->t_args, &a, sizeof a, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d->t_start, start, sizeof start, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d->t_gx, &gx, sizeof gx, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d->t_rows, &rows, sizeof rows, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d->t_n, &one, sizeof one, cudaMemcpyHostToDevice));
+    return SWE_OK;
+}
+
+swe::BatchTable own_table(const swe_domain *d) {
+    swe::BatchTable t;
+    t.args = d->t_args;
+    t.tile_start = d->t_start;
+    t.grid_x = d->t_gx;
+    t.rows = d->t_rows;
+    t.n_domains = d->t_n;
+    return t;
 }
 
 int upload_plane(swe_domain *d, void *dst, const void *src, int rows, int cols,
@@ -185,6 +232,7 @@ int create_impl(const swe_domain_desc *dd, const swe_params *p, void *stream, sw
     long long align = 128 / (long long)d->esz;
     d->pitch = round_up(d->nx, align);
     d->cpitch = round_up(d->nx + 1, align);
+    if (d->cpitch * (d->ny + 1) >= (1LL << 31)) return SWE_ERR_INVALID_ARG;   // 32-bit offsets
     const size_t pb = d->plane_bytes();
     for (int b = 0; b < 2; b++)
         for (int k = 0; k < 3; k++)
@@ -202,6 +250,12 @@ int create_impl(const swe_domain_desc *dd, const swe_params *p, void *stream, sw
     d->f_const = dd->f_const;
     d->th_const = dd->theta_const;
     if (!(d->ctl = (StepCtl *)d->dalloc(sizeof(StepCtl)))) return SWE_ERR_OOM;
+    if (d->fast()) {
+        if (!(d->t_args = (swe::StageArgs<float> *)d->dalloc(sizeof(swe::StageArgs<float>))) ||
+            !(d->t_start = (int *)d->dalloc(2 * sizeof(int))) || !(d->t_gx = (int *)d->dalloc(sizeof(int))) ||
+            !(d->t_rows = (int *)d->dalloc(sizeof(int))) || !(d->t_n = (int *)d->dalloc(sizeof(int))))
+            return SWE_ERR_OOM;
+    }
     int nb = swe::diag_blocks(d->nx, d->ny);
     if (!(d->diag_partials = (double *)d->dalloc((size_t)nb * 2 * sizeof(double)))) return SWE_ERR_OOM;
     if (!(d->diag_out = (double *)d->dalloc(2 * sizeof(double)))) return SWE_ERR_OOM;
@@ -221,6 +275,7 @@ int create_impl(const swe_domain_desc *dd, const swe_params *p, void *stream, sw
     cudaError_t e = swe::launch_ctl_init(d->ctl, p->t0, d->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if ((rc = init_clock(d, p->t0, p->dt_fixed > 0 ? p->dt_fixed : 0.0, 0))) return rc;
+    if ((rc = upload_table(d))) return rc;
     if (dd->src_is_device == 0) CK(cudaStreamSynchronize(d->stream));
     return SWE_OK;
 }
@@ -245,11 +300,7 @@ int validate(const swe_domain_desc *d, const swe_params *p) {
     return SWE_OK;
 }
 
-void *plane_of(swe_domain *d, int field) {
-    if (field >= SWE_ETA && field <= SWE_HV) return d->q[d->cur][field];
-    if (field >= SWE_COMP_ETA && field <= SWE_COMP_HV) return d->comp[field - SWE_COMP_ETA];
-    return nullptr;
-}
+
 
 }  // namespace
 
@@ -333,6 +384,7 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times, c
     }
     // the old series may still be read by queued kernels: drain first
     CK(cudaStreamSynchronize(h->stream));
+    h->drop_graph();
     if (kind == SWE_FORCING_WIND) {
         h->dfree(h->wind); h->dfree(h->wind_t);
         h->wind = nf; h->wind_t = nt; h->wind_n = n_frames; h->wind_n1 = n1; h->wind_n2 = n2;
@@ -342,6 +394,7 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times, c
     }
     int rc = refresh_brackets(h);
     if (rc) return rc;
+    if ((rc = upload_table(h))) return rc;      // new forcing pointers
     CK(cudaStreamSynchronize(h->stream));
     return SWE_OK;
 }
@@ -357,13 +410,35 @@ int step_check(swe_handle h, int n_steps) {
     return SWE_OK;
 }
 
-int launch_part(swe_handle h, int part) {
+int launch_part_on(swe_handle h, int part, cudaStream_t st) {
     cudaError_t e;
-    if (h->prec == SWE_F64) e = swe::launch_step_ref_part(make_args<double>(h), h->stream, part, false);
-    else if (h->fast()) e = swe::launch_step_fast_part(make_args<float>(h), h->stream, part, h->prec == SWE_F32_KAHAN);
-    else e = swe::launch_step_ref_part(make_args<float>(h), h->stream, part, h->prec == SWE_F32_KAHAN);
+    if (h->prec == SWE_F64) e = swe::launch_step_ref_part(make_args<double>(h), st, part, false);
+    else if (h->fast()) e = swe::launch_batch_stage(own_table(h), h->t_tiles, part + 1, st);
+    else e = swe::launch_step_ref_part(make_args<float>(h), st, part, h->prec == SWE_F32_KAHAN);
     if (e != cudaSuccess) return cuda_fail(e);
-    h->launches++;
+    return SWE_OK;
+}
+
+int launch_part(swe_handle h, int part) {
+    int rc = launch_part_on(h, part, h->stream);
+    if (!rc) h->launches++;
+    return rc;
+}
+
+int ensure_graph(swe_handle h) {
+    if (h->graph) return SWE_OK;
+    if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = SWE_OK;
+    for (int s = 0; s < swe_domain::kGraphSteps && !rc; s++)
+        for (int p = 0; p < h->parts() && !rc; p++) rc = launch_part_on(h, p, h->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(e); }
     return SWE_OK;
 }
 
@@ -373,11 +448,17 @@ int swe_step(swe_handle h, int n_steps) {
     int rc = step_check(h, n_steps);
     if (rc) return rc;
     const int parts = h->parts();
-    for (int s = 0; s < n_steps; s++) {
+    const int G = swe_domain::kGraphSteps;
+    if (n_steps >= G) {
+        if ((rc = ensure_graph(h))) return rc;
+        for (; n_steps >= G; n_steps -= G) {
+            CK(cudaGraphLaunch(h->graph, h->stream));
+            h->launches += (long long)G * parts;
+        }
+    }
+    for (int s = 0; s < n_steps; s++)
         for (int p = 0; p < parts; p++)
             if ((rc = launch_part(h, p))) return rc;
-        h->cur ^= 1;
-    }
     return SWE_OK;
 }
 
@@ -409,7 +490,6 @@ int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
             if ((rc = launch_part(h, p))) return rc;
             CK(cudaEventRecord(h->events[k++], h->stream));
         }
-        h->cur ^= 1;
     }
     CK(cudaEventSynchronize(h->events[need - 1]));
     for (size_t q = 0; q < need / 2; q++) CK(cudaEventElapsedTime(&ms[q], h->events[2 * q], h->events[2 * q + 1]));
@@ -418,13 +498,41 @@ int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
 
 int swe_read_state(swe_handle h, int field, void *dst, int dst_is_device) {
     if (!h || !dst) return SWE_ERR_INVALID_ARG;
-    void *src = plane_of(h, field);
-    if (!src) return field >= SWE_COMP_ETA && field <= SWE_COMP_HV ? SWE_ERR_UNSUPPORTED : SWE_ERR_INVALID_ARG;
-    CK(cudaMemcpy2DAsync(dst, (size_t)h->nx * h->esz, src, (size_t)h->pitch * h->esz,
-                         (size_t)h->nx * h->esz, (size_t)h->ny,
-                         dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    const void *src = nullptr;
+    if (field >= SWE_COMP_ETA && field <= SWE_COMP_HV) {
+        src = h->comp[field - SWE_COMP_ETA];
+        if (!src) return SWE_ERR_UNSUPPORTED;
+    } else if (field < SWE_ETA || field > SWE_HV) {
+        return SWE_ERR_INVALID_ARG;
+    }
+    if (src) {
+        CK(cudaMemcpy2DAsync(dst, (size_t)h->nx * h->esz, src, (size_t)h->pitch * h->esz,
+                             (size_t)h->nx * h->esz, (size_t)h->ny,
+                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    } else if (dst_is_device) {
+        // the current buffer is known only to the device: copy by kernel
+        cudaError_t e = h->prec == SWE_F64
+            ? swe::launch_read_plane<double>(h->ctl, (const double *)h->q[0][field], (const double *)h->q[1][field],
+                                             h->pitch, h->nx, h->ny, (double *)dst, h->stream)
+            : swe::launch_read_plane<float>(h->ctl, (const float *)h->q[0][field], (const float *)h->q[1][field],
+                                            h->pitch, h->nx, h->ny, (float *)dst, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    } else {
+        int par = 0;
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaMemcpy(&par, &h->ctl->parity, sizeof par, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy2D(dst, (size_t)h->nx * h->esz, h->q[par & 1][field], (size_t)h->pitch * h->esz,
+                        (size_t)h->nx * h->esz, (size_t)h->ny, cudaMemcpyDeviceToHost));
+    }
     if (!dst_is_device) CK(cudaStreamSynchronize(h->stream));
     return SWE_OK;
+}
+
+int swe_set_end_time(swe_handle h, double t_end) {
+    if (!h || !(t_end >= 0.0) || !std::isfinite(t_end)) return SWE_ERR_INVALID_ARG;
+    cudaError_t e = swe::launch_set_end(h->ctl, t_end, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return refresh_brackets(h);
 }
 
 int swe_write_state(swe_handle h, int field, const void *src, int src_is_device) {
@@ -464,6 +572,8 @@ int swe_get_info(swe_handle h, swe_info *out) {
     out->error_step = c.err_step;
     out->max_speed = c.last_speed;
     out->launches = h->launches;
+    out->done = c.done;
+    out->t_end = c.t_end;
     if (c.err != 0) {
         h->sticky_numeric = true;
         return SWE_ERR_NUMERIC;
@@ -487,6 +597,261 @@ int swe_destroy_domain(swe_handle h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     h->free_all();
     delete h;
+    return e == cudaSuccess ? SWE_OK : cuda_fail(e);
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batches: many FP32 domains advanced by one persistent launch per stage
+
+struct swe_batch {
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int cap = 0;
+    std::vector<swe_handle> doms;
+    std::vector<int> rows;          // tile height per domain
+    int rows_choice = 0;            // 0: autotune on the next long step
+    bool tuned = false;
+    // device tables (capacity `cap`)
+    swe::StageArgs<float> *d_args = nullptr;
+    int *d_tile_start = nullptr, *d_grid_x = nullptr, *d_rows = nullptr, *d_n = nullptr;
+    int *d_done = nullptr;
+    double *d_t = nullptr;
+    int blocks = 0;
+    cudaGraphExec_t graph = nullptr;
+    static constexpr int kGraphSteps = 8;
+    long long launches = 0;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+const int kTuneRows[] = {8, 16, 32, 64};
+
+int batch_upload(swe_batch *b) {
+    const int n = (int)b->doms.size();
+    std::vector<swe::StageArgs<float>> args(n);
+    std::vector<int> start(n + 1, 0), gx(n), rows(n);
+    for (int k = 0; k < n; k++) {
+        args[k] = make_args<float>(b->doms[k]);
+        rows[k] = b->rows[k];
+        start[k + 1] = start[k] + swe::fast_tiles(b->doms[k]->nx, b->doms[k]->ny, rows[k], &gx[k]);
+    }
+    // synchronous copies: the graph reads these tables; nothing is in flight
+    CK(cudaStreamSynchronize(b->stream));
+    if (n) {
+        CK(cudaMemcpy(b->d_args, args.data(), sizeof(args[0]) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->d_grid_x, gx.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->d_rows, rows.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(b->d_tile_start, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_n, &n, sizeof(int), cudaMemcpyHostToDevice));
+    return SWE_OK;
+}
+
+swe::BatchTable batch_table(const swe_batch *b) {
+    swe::BatchTable t;
+    t.args = b->d_args;
+    t.tile_start = b->d_tile_start;
+    t.grid_x = b->d_grid_x;
+    t.rows = b->d_rows;
+    t.n_domains = b->d_n;
+    return t;
+}
+
+int batch_launch_step(swe_batch *b, cudaStream_t st) {
+    for (int stage = 1; stage <= 2; stage++) {
+        cudaError_t e = swe::launch_batch_stage(batch_table(b), b->blocks, stage, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return SWE_OK;
+}
+
+int batch_ensure_graph(swe_batch *b) {
+    if (b->graph) return SWE_OK;
+    if (!b->capture_stream) CK(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = SWE_OK;
+    for (int s = 0; s < swe_batch::kGraphSteps && !rc; s++) rc = batch_launch_step(b, b->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e); }
+    return SWE_OK;
+}
+
+int batch_set_rows_all(swe_batch *b, int rows) {
+    for (size_t k = 0; k < b->doms.size(); k++)
+        b->rows[k] = rows > 0 ? rows : swe::fast_rows(b->doms[k]->nx, b->doms[k]->ny);
+    return batch_upload(b);
+}
+
+// Autotuner: time two batch steps with every candidate tile height and keep
+// the fastest. The steps are real steps of the forecast (the result does
+// not depend on the tiling), so tuning costs no extra simulation.
+int batch_tune(swe_batch *b, int *steps_used) {
+    *steps_used = 0;
+    if (b->doms.empty()) return SWE_OK;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_rows = kTuneRows[0];
+    for (int rows : kTuneRows) {
+        int rc = batch_set_rows_all(b, rows);
+        if (!rc) rc = batch_launch_step(b, b->stream);      // settle
+        if (!rc) CK(cudaEventRecord(e0, b->stream));
+        if (!rc) rc = batch_launch_step(b, b->stream);
+        if (!rc) CK(cudaEventRecord(e1, b->stream));
+        if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        *steps_used += 2;
+        b->launches += 4;
+        if (ms < best) { best = ms; best_rows = rows; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->rows_choice = best_rows;
+    b->tuned = true;
+    return batch_set_rows_all(b, best_rows);
+}
+
+}  // namespace
+
+extern "C" {
+
+int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out) {
+    if (!out || max_domains < 1 || max_domains > (1 << 20)) return SWE_ERR_INVALID_ARG;
+    *out = nullptr;
+    swe_batch *b = new (std::nothrow) swe_batch();
+    if (!b) return SWE_ERR_OOM;
+    b->stream = (cudaStream_t)stream;
+    b->cap = max_domains;
+    bool ok = cudaMalloc(&b->d_args, sizeof(swe::StageArgs<float>) * max_domains) == cudaSuccess &&
+              cudaMalloc(&b->d_tile_start, sizeof(int) * (max_domains + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_grid_x, sizeof(int) * max_domains) == cudaSuccess &&
+              cudaMalloc(&b->d_rows, sizeof(int) * max_domains) == cudaSuccess &&
+              cudaMalloc(&b->d_n, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_done, sizeof(int) * max_domains) == cudaSuccess &&
+              cudaMalloc(&b->d_t, sizeof(double) * max_domains) == cudaSuccess;
+    if (ok) ok = batch_upload(b) == SWE_OK;
+    if (ok) b->blocks = swe::batch_grid_blocks();
+    if (!ok) {
+        cudaFree(b->d_args); cudaFree(b->d_tile_start); cudaFree(b->d_grid_x); cudaFree(b->d_rows);
+        cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t);
+        delete b;
+        return SWE_ERR_OOM;
+    }
+    *out = b;
+    return SWE_OK;
+}
+
+int swe_batch_add(swe_batch_handle b, swe_handle d) {
+    if (!b || !d) return SWE_ERR_INVALID_ARG;
+    if (d->prec == SWE_F64 || !d->fast()) return SWE_ERR_UNSUPPORTED;
+    if ((int)b->doms.size() >= b->cap) return SWE_ERR_INVALID_ARG;
+    for (swe_handle x : b->doms)
+        if (x == d) return SWE_ERR_INVALID_ARG;
+    if (step_check(d, 0)) return step_check(d, 0);
+    CK(cudaStreamSynchronize(d->stream));      // creation and uploads finished
+    b->doms.push_back(d);
+    b->rows.push_back(b->rows_choice > 0 ? b->rows_choice : swe::fast_rows(d->nx, d->ny));
+    return batch_upload(b);
+}
+
+int swe_batch_remove(swe_batch_handle b, swe_handle d) {
+    if (!b || !d) return SWE_ERR_INVALID_ARG;
+    for (size_t k = 0; k < b->doms.size(); k++)
+        if (b->doms[k] == d) {
+            b->doms.erase(b->doms.begin() + (long)k);
+            b->rows.erase(b->rows.begin() + (long)k);
+            return batch_upload(b);             // also drains the batch stream
+        }
+    return SWE_ERR_INVALID_ARG;
+}
+
+int swe_batch_size(swe_batch_handle b) { return b ? (int)b->doms.size() : SWE_ERR_INVALID_ARG; }
+
+int swe_batch_set_rows(swe_batch_handle b, int rows) {
+    if (!b || rows < 0 || rows > 1024) return SWE_ERR_INVALID_ARG;
+    b->rows_choice = rows;
+    b->tuned = rows > 0;
+    return batch_set_rows_all(b, rows);
+}
+
+int swe_batch_rows(swe_batch_handle b) { return b ? b->rows_choice : SWE_ERR_INVALID_ARG; }
+
+int swe_batch_step(swe_batch_handle b, int n_steps) {
+    if (!b || n_steps < 0) return SWE_ERR_INVALID_ARG;
+    if (b->doms.empty() || n_steps == 0) return SWE_OK;
+    int rc;
+    const int ncand = (int)(sizeof kTuneRows / sizeof kTuneRows[0]);
+    if (!b->tuned && n_steps >= 4 * ncand) {
+        int used = 0;
+        if ((rc = batch_tune(b, &used))) return rc;
+        n_steps -= used;
+    }
+    const int G = swe_batch::kGraphSteps;
+    if (n_steps >= G) {
+        if ((rc = batch_ensure_graph(b))) return rc;
+        for (; n_steps >= G; n_steps -= G) {
+            CK(cudaGraphLaunch(b->graph, b->stream));
+            b->launches += 2LL * G;
+        }
+    }
+    for (; n_steps > 0; n_steps--) {
+        if ((rc = batch_launch_step(b, b->stream))) return rc;
+        b->launches += 2;
+    }
+    return SWE_OK;
+}
+
+int swe_batch_step_serial(swe_batch_handle b, int n_steps) {
+    if (!b || n_steps < 0) return SWE_ERR_INVALID_ARG;
+    for (int s = 0; s < n_steps; s++)
+        for (swe_handle d : b->doms)
+            for (int p = 0; p < d->parts(); p++) {
+                int rc = launch_part_on(d, p, b->stream);
+                if (rc) return rc;
+                b->launches++;
+            }
+    return SWE_OK;
+}
+
+int swe_batch_sync(swe_batch_handle b) {
+    if (!b) return SWE_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    return SWE_OK;
+}
+
+int swe_batch_poll(swe_batch_handle b, int *done, double *t, int capacity) {
+    if (!b || capacity < (int)b->doms.size()) return SWE_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k < b->doms.size(); k++) {
+        swe::StepCtl c;
+        CK(cudaMemcpy(&c, b->doms[k]->ctl, sizeof c, cudaMemcpyDeviceToHost));
+        if (done) done[k] = c.done;
+        if (t) t[k] = c.t;
+    }
+    return SWE_OK;
+}
+
+long long swe_batch_launches(swe_batch_handle b) { return b ? b->launches : SWE_ERR_INVALID_ARG; }
+
+int swe_batch_destroy(swe_batch_handle b) {
+    if (!b) return SWE_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    cudaFree(b->d_args); cudaFree(b->d_tile_start); cudaFree(b->d_grid_x); cudaFree(b->d_rows);
+    cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t);
+    delete b;
     return e == cudaSuccess ? SWE_OK : cuda_fail(e);
 }
 

@@ -16,12 +16,14 @@ __device__ __forceinline__ T desing(T h, T kappa, T half_inv_kappa) {
     return h < T(0) ? -r : r;
 }
 
-// Generalised minmod of (theta*backward, central, theta*forward).
+// Generalised minmod of (theta*backward, central, theta*forward): the
+// smallest when all three are positive, the largest when all are negative,
+// else zero. Written branch-free as max(0, min3) + min(0, max3), which gives
+// exactly those values (one of the two terms is always an exact zero).
 template <typename T>
 __device__ __forceinline__ T minmod3(T a, T b, T c) {
-    if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
-    if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
-    return T(0);
+    const T lo = fmin(a, fmin(b, c)), hi = fmax(a, fmax(b, c));
+    return fmax(T(0), lo) + fmin(T(0), hi);
 }
 
 // One cell as seen by the stencil: state, bilinear bathymetry at the cell
@@ -311,7 +313,7 @@ __device__ __forceinline__ void bracket(const double *times, int n, double t, in
 __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
                              const ForcingDev &wind, double speed, int mode) {
     ctl->last_speed = speed;
-    if (mode == 1) { ctl->t += ctl->dt; ctl->step += 1; }
+    if (mode == 1) { ctl->t += ctl->dt; ctl->step += 1; ctl->parity ^= 1; }
     if (clk.dt_fixed > 0.0) {
         ctl->dt = clk.dt_fixed;
     } else if (mode == 0 || (mode == 1 && ctl->step % clk.dt_every == 0)) {
@@ -321,6 +323,11 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
             ctl->err = ERR_NUMERIC;
             ctl->err_step = ctl->step;
         }
+    }
+    // a forecast horizon: clip the last step to land on t_end, then stop
+    if (ctl->t_end > 0.0) {
+        if (ctl->t >= ctl->t_end * (1.0 - 1e-14)) ctl->done = 1;
+        else if (ctl->t + ctl->dt > ctl->t_end) ctl->dt = ctl->t_end - ctl->t;
     }
     for (int s = 0; s < 2; s++) {
         double tt = ctl->t + (s ? ctl->dt : 0.0);
@@ -339,6 +346,9 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
             ctl->tau[s][0] = k * wx;
             ctl->tau[s][1] = k * wy;
         }
+        ctl->bs_f[s] = (float)ctl->bs[s];
+        ctl->tau_f[s][0] = (float)ctl->tau[s][0];
+        ctl->tau_f[s][1] = (float)ctl->tau[s][1];
     }
 }
 

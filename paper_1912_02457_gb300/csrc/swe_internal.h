@@ -22,6 +22,8 @@ struct StepCtl {
     long long step;           // steps taken
     double tau[2][2];         // uniform wind stress at stage-1 / stage-2 time
     double bs[2];             // boundary frame weight s at stage-1 / stage-2 time
+    float bs_f[2];            // the same, rounded once for FP32 kernels
+    float tau_f[2][2];        // uniform wind stress rounded once for FP32 kernels
     double ws[2];             // wind frame weight s
     int bk[2];                // boundary frame index at stage-1 / stage-2 time
     int wk[2];                // wind frame index
@@ -32,6 +34,9 @@ struct StepCtl {
     int err;                  // sticky error code
     int err_cell;             // first offending cell, -1 if none
     long long err_step;
+    int parity;               // which state buffer holds Q^n (flipped per step)
+    int done;                 // 1 once t reached t_end: steps become no-ops
+    double t_end;             // end of the forecast (0: none); the last dt is clipped
 };
 
 // Clock policy, copied by value into the finalise kernels.
@@ -60,17 +65,24 @@ struct StageArgs {
     int bc[4];
     const T *H, *f, *th;      // corner depths; f/theta planes or NULL
     T f_const, th_const;
-    const T *qin[3];          // state at the start of the step
-    T *qout[3];               // state after the step (stage 2)
+    T *q[2][3];               // ping-pong state buffers; ctl->parity selects Q^n
     T *d1[3];                 // stage-1 increment Q* - Q^n
     T *comp[3];               // Kahan compensation (F32_KAHAN) or NULL
     ForcingDev bnd, wind;
     int frs_width;
     double frs_alpha[kMaxFrs];
+    float frs_alpha_f[kMaxFrs];   // the same weights rounded once for FP32 kernels
     StepCtl *ctl;
     ClockParams clk;
-    float *partials;          // per-block maxima of the fused finalise
-    int nblocks;              // blocks of the stage-2 launch
+};
+
+// Device-resident tile table of a batch of FP32 domains (persistent kernel).
+struct BatchTable {
+    const StageArgs<float> *args;   // per domain
+    const int *tile_start;          // n+1 prefix sums of tiles per domain
+    const int *grid_x;              // 28-column strips per row of each domain
+    const int *rows;                // tile height of each domain
+    const int *n_domains;           // current number of domains (device)
 };
 
 }  // namespace swe

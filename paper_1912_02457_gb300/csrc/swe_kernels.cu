@@ -30,7 +30,7 @@ __device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c)
 // mirrored interior cell (faces swapped), state from the external frames
 // at the stage time (Section 3.6).
 template <typename T, int STAGE>
-__device__ __forceinline__ void load_cell(const StageArgs<T> &a, int i, int j, Cell<T> &c) {
+__device__ __forceinline__ void load_cell(const StageArgs<T> &a, int par, int i, int j, Cell<T> &c) {
     const int nx = a.nx, ny = a.ny;
     int si = i, sj = j, e = -1, row = 0;
     if (i < 0)        { e = EDGE_W; si = -i - 1;         row = -i - 1; }
@@ -55,7 +55,7 @@ __device__ __forceinline__ void load_cell(const StageArgs<T> &a, int i, int j, C
     T th = a.th ? a.th[s] : a.th_const;
     sincos_t(th, &c.st, &c.ct);
     if (e < 0) {
-        c.eta = a.qin[0][s]; c.hu = a.qin[1][s]; c.hv = a.qin[2][s];
+        c.eta = a.q[par][0][s]; c.hu = a.q[par][1][s]; c.hv = a.q[par][2][s];
         if (STAGE == 2) { c.eta += a.d1[0][s]; c.hu += a.d1[1][s]; c.hv += a.d1[2][s]; }
     } else {
         int k = e >= EDGE_W ? j : i;
@@ -96,24 +96,26 @@ __device__ __forceinline__ void speed_atomic_max(StepCtl *ctl, double v) {
 template <typename T, int STAGE, bool KAHAN>
 __global__ void __launch_bounds__(256) stage_ref_kernel(StageArgs<T> a) {
     __shared__ T sh[32];
+    if (a.ctl->done) return;                      // forecast horizon reached
+    const int par = a.ctl->parity;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const bool act = i < a.nx && j < a.ny;
     T speed = T(0);
     Cell<T> C;
     C.land = true;
-    if (act) load_cell<T, STAGE>(a, i, j, C);
+    if (act) load_cell<T, STAGE>(a, par, i, j, C);
     if (act && !C.land) {
         const T g = a.g, kappa = a.kappa, hik = a.half_inv_kappa;
         Cell<T> W2, W1, E1, E2, S2, S1, N1, N2;
-        load_cell<T, STAGE>(a, i - 2, j, W2);
-        load_cell<T, STAGE>(a, i - 1, j, W1);
-        load_cell<T, STAGE>(a, i + 1, j, E1);
-        load_cell<T, STAGE>(a, i + 2, j, E2);
-        load_cell<T, STAGE>(a, i, j - 2, S2);
-        load_cell<T, STAGE>(a, i, j - 1, S1);
-        load_cell<T, STAGE>(a, i, j + 1, N1);
-        load_cell<T, STAGE>(a, i, j + 2, N2);
+        load_cell<T, STAGE>(a, par, i - 2, j, W2);
+        load_cell<T, STAGE>(a, par, i - 1, j, W1);
+        load_cell<T, STAGE>(a, par, i + 1, j, E1);
+        load_cell<T, STAGE>(a, par, i + 2, j, E2);
+        load_cell<T, STAGE>(a, par, i, j - 2, S2);
+        load_cell<T, STAGE>(a, par, i, j - 1, S1);
+        load_cell<T, STAGE>(a, par, i, j + 1, N1);
+        load_cell<T, STAGE>(a, par, i, j + 2, N2);
 
         Face<T> cE, cW, cN, cS, L, R;
         T Fw[3], Fe[3], Gs[3], Gn[3];
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) stage_ref_kernel(StageArgs<T> a) {
             a.d1[2][s] = (dt * m2 - dt * S * C.hv) * den;
         } else {
             // Q^{n+1} - Q^n = (D1 + dt M(Q*) - dt S Q^n) / 2 / (1 + dt S / 2)
-            T q0 = a.qin[0][s], q1 = a.qin[1][s], q2 = a.qin[2][s];
+            T q0 = a.q[par][0][s], q1 = a.q[par][1][s], q2 = a.q[par][2][s];
             T D0 = a.d1[0][s], D1 = a.d1[1][s], D2 = a.d1[2][s];
             T den = T(1) / (T(1) + T(0.5) * dt * S);
             T de0 = T(0.5) * (D0 + dt * m0);
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(256) stage_ref_kernel(StageArgs<T> a) {
                     q0 += al * (x0 - q0); q1 += al * (x1 - q1); q2 += al * (x2 - q2);
                 }
             }
-            a.qout[0][s] = q0; a.qout[1][s] = q1; a.qout[2][s] = q2;
+            a.q[par ^ 1][0][s] = q0; a.q[par ^ 1][1][s] = q1; a.q[par ^ 1][2][s] = q2;
             if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
             if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, j * a.nx + i);
             speed = cell_speed(a, q0, q1, q2, C.Hbar);
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(256) stage_ref_kernel(StageArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(256) speed_kernel(StageArgs<T> a) {
     __shared__ T sh[32];
+    const int par = a.ctl->parity;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     T speed = T(0);
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(256) speed_kernel(StageArgs<T> a) {
         const T L = T(kLand);
         if (!((c00 == L) | (c10 == L) | (c01 == L) | (c11 == L))) {
             const long long s = (long long)j * a.pitch + i;
-            speed = cell_speed(a, a.qin[0][s], a.qin[1][s], a.qin[2][s],
+            speed = cell_speed(a, a.q[par][0][s], a.q[par][1][s], a.q[par][2][s],
                                T(0.25) * (c00 + c10 + c01 + c11));
         }
     }
@@ -237,6 +240,7 @@ __global__ void __launch_bounds__(256) speed_kernel(StageArgs<T> a) {
 
 template <typename T>
 __global__ void clock_kernel(StepCtl *ctl, ClockParams clk, ForcingDev bnd, ForcingDev wind, int mode) {
+    if (mode == 1 && ctl->done) return;
     double speed = sizeof(T) == 4 ? (double)__uint_as_float(ctl->speed32)
                                   : __longlong_as_double((long long)ctl->speed64);
     ctl->speed32 = 0u;
@@ -247,6 +251,7 @@ __global__ void clock_kernel(StepCtl *ctl, ClockParams clk, ForcingDev bnd, Forc
 __global__ void set_clock_kernel(StepCtl *ctl, double t, double dt, long long step) {
     ctl->t = t;
     ctl->step = step;
+    ctl->done = 0;
     if (dt > 0.0) ctl->dt = dt;
     ctl->speed32 = 0u;
     ctl->speed64 = 0ull;
@@ -260,12 +265,32 @@ __global__ void init_ctl_kernel(StepCtl *ctl, double t0) {
     *ctl = z;
 }
 
+// Copy one plane of the current state (buffer chosen by the device-side
+// parity) into a dense nx*ny destination.
+template <typename T>
+__global__ void read_plane_kernel(const StepCtl *ctl, const T *q0, const T *q1, long long pitch,
+                                  int nx, int ny, T *dst) {
+    const T *src = ctl->parity ? q1 : q0;
+    long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long j = k / nx, i = k - j * nx;
+        dst[k] = src[j * pitch + i];
+    }
+}
+
+__global__ void set_end_kernel(StepCtl *ctl, double t_end) {
+    ctl->t_end = t_end;
+    ctl->done = 0;
+}
+
 // ---------------------------------------------------------------------------
 // FP64 diagnostics: deterministic two-pass block sums
 
 template <typename T>
 __global__ void __launch_bounds__(256) diag_partial_kernel(StageArgs<T> a, double *partials) {
     __shared__ double sh[2][8];
+    const int par = a.ctl->parity;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     double m = 0.0, en = 0.0;
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(StageArgs<T> a, doubl
         const T L = T(kLand);
         if (!((c00 == L) | (c10 == L) | (c01 == L) | (c11 == L))) {
             const long long s = (long long)j * a.pitch + i;
-            double e = (double)a.qin[0][s], u = (double)a.qin[1][s], v = (double)a.qin[2][s];
+            double e = (double)a.q[par][0][s], u = (double)a.q[par][1][s], v = (double)a.q[par][2][s];
             double Hb = 0.25 * ((double)c00 + (double)c10 + (double)c01 + (double)c11);
             double k = (double)a.kappa;
             double h = e + Hb;
@@ -362,6 +387,23 @@ cudaError_t launch_init_clock(const StageArgs<T> &a, cudaStream_t st, double t, 
 template <typename T>
 cudaError_t launch_refresh_brackets(const StageArgs<T> &a, cudaStream_t st) {
     clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long long pitch,
+                              int nx, int ny, T *dst, cudaStream_t st) {
+    long long n = (long long)nx * ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    read_plane_kernel<T><<<blocks, 256, 0, st>>>(ctl, q0, q1, pitch, nx, ny, dst);
+    return cudaGetLastError();
+}
+template cudaError_t launch_read_plane<float>(const StepCtl *, const float *, const float *, long long, int, int, float *, cudaStream_t);
+template cudaError_t launch_read_plane<double>(const StepCtl *, const double *, const double *, long long, int, int, double *, cudaStream_t);
+
+cudaError_t launch_set_end(StepCtl *ctl, double t_end, cudaStream_t st) {
+    set_end_kernel<<<1, 1, 0, st>>>(ctl, t_end);
     return cudaGetLastError();
 }
 

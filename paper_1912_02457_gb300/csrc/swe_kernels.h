@@ -17,12 +17,20 @@ template <typename T>
 cudaError_t launch_diagnostics(const StageArgs<T> &a, double *partials, double *out,
                                cudaStream_t st);
 cudaError_t launch_ctl_init(StepCtl *ctl, double t0, cudaStream_t st);
+cudaError_t launch_set_end(StepCtl *ctl, double t_end, cudaStream_t st);
+template <typename T>
+cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long long pitch,
+                              int nx, int ny, T *dst, cudaStream_t st);
 
 // FP32 sliding-window stage kernels (swe_stage_fast.cu): stage 1, then
-// stage 2 with the fused CFL reduction and clock update.
+// stage 2 with the fused CFL reduction and clock update. A single domain
+// runs through the same kernel as a batch, with a one-entry tile table.
 int fast_step_parts();
 const char *fast_part_name(int part);
-cudaError_t launch_step_fast_part(const StageArgs<float> &a, cudaStream_t st, int part, bool kahan);
+int fast_rows(int nx, int ny);
+int fast_tiles(int nx, int ny, int rows, int *grid_x);
+int batch_grid_blocks();
+cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st);
 int diag_blocks(int nx, int ny);
 
 }  // namespace swe

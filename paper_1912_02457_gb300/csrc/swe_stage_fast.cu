@@ -24,6 +24,12 @@ namespace {
 
 constexpr int kStrip = 28;           // output columns per warp
 constexpr int kWarps = 4;            // warps per block
+#ifndef SWE_MIN_BLOCKS
+#define SWE_MIN_BLOCKS 4             // resident blocks per SM the register budget targets
+#endif
+#ifndef SWE_FORCE_ROWS
+#define SWE_FORCE_ROWS 0             // > 0: fixed tile height (tuning builds)
+#endif
 
 __device__ __forceinline__ void bnd_pos_f(int k, int n, int nb, int &k0, int &k1, float &w) {
     float p = (k + 0.5f) * (float)nb / (float)n - 0.5f;
@@ -47,7 +53,7 @@ __device__ __forceinline__ void bnd_state_f(const StageArgs<float> &a, int e, in
     float w;
     bnd_pos_f(k, n, nb, k0, k1, w);
     int fk = a.ctl->bk[stage];
-    float s = (float)a.ctl->bs[stage];
+    float s = a.ctl->bs_f[stage];
     long long fs = 12LL * (F.n1 + F.n2);
     const float *A = F.frames + (long long)fk * fs + off + (long long)(r * 3) * nb;
     const float *B = F.n > 1 ? A + fs : A;
@@ -64,7 +70,7 @@ __device__ __forceinline__ void bnd_state_f(const StageArgs<float> &a, int e, in
 // wall the cell is land; outside a nested edge it is the ghost of
 // Section 3.6 (mirrored statics, external state).
 template <int STAGE>
-__device__ __forceinline__ void load_cell_f(const StageArgs<float> &a, int i, int r, Cell<float> &c) {
+__device__ __forceinline__ void load_cell_f(const StageArgs<float> &a, int par, int i, int r, Cell<float> &c) {
     const int nx = a.nx, ny = a.ny;
     int si = i, sj = r, e = -1, row = 0;
     const bool ox = i < 0 || i >= nx, oy = r < 0 || r >= ny;
@@ -94,12 +100,57 @@ __device__ __forceinline__ void load_cell_f(const StageArgs<float> &a, int i, in
     float th = a.th ? __ldg(a.th + s) : a.th_const;
     __sincosf(th, &c.st, &c.ct);
     if (e < 0) {
-        c.eta = a.qin[0][s]; c.hu = a.qin[1][s]; c.hv = a.qin[2][s];
+        c.eta = a.q[par][0][s]; c.hu = a.q[par][1][s]; c.hv = a.q[par][2][s];
         if (STAGE == 2) { c.eta += a.d1[0][s]; c.hu += a.d1[1][s]; c.hv += a.d1[2][s]; }
     } else {
         int k = e >= EDGE_W ? r : i;
         bnd_state_f(a, e, row, k, STAGE - 1, c.eta, c.hu, c.hv);
     }
+    make_prim(c, a.kappa, a.half_inv_kappa);
+}
+
+// Raw loads of one cell of the next row, issued one iteration ahead of use
+// so their latency hides behind the current row's arithmetic. `fast`: an
+// interior cell (ghosts and out-of-range cells take load_cell_f).
+template <int STAGE>
+struct RawCell {
+    bool fast;
+    float c00, c10, c01, c11, f, th, q0, q1, q2, d0, d1, d2;
+};
+
+template <int STAGE>
+__device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, int i, int r,
+                                           RawCell<STAGE> &w) {
+    w.fast = (unsigned)i < (unsigned)a.nx && (unsigned)r < (unsigned)a.ny;
+    if (!w.fast) return;
+    // offsets fit in 32 bits (checked when the domain is created)
+    const int cp = (int)a.cpitch;
+    const float *H = a.H + (r * cp + i);
+    w.c00 = __ldg(H); w.c10 = __ldg(H + 1); w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
+    const int s = r * (int)a.pitch + i;
+    w.f = a.f ? __ldg(a.f + s) : a.f_const;
+    w.th = a.th ? __ldg(a.th + s) : a.th_const;
+    w.q0 = __ldg(a.q[par][0] + s); w.q1 = __ldg(a.q[par][1] + s); w.q2 = __ldg(a.q[par][2] + s);
+    if (STAGE == 2) { w.d0 = __ldg(a.d1[0] + s); w.d1 = __ldg(a.d1[1] + s); w.d2 = __ldg(a.d1[2] + s); }
+}
+
+template <int STAGE>
+__device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int par, int i, int r,
+                                            const RawCell<STAGE> &w, Cell<float> &c) {
+    if (!w.fast) { load_cell_f<STAGE>(a, par, i, r, c); return; }
+    c.land = (w.c00 == kLand) | (w.c10 == kLand) | (w.c01 == kLand) | (w.c11 == kLand);
+    if (c.land) {
+        c.eta = c.hu = c.hv = c.Hbar = c.HE = c.HW = c.HN = c.HS = 0.f;
+        c.f = c.ct = c.st = c.hbar = c.hs = c.u = c.v = c.fvx = c.fuy = 0.f;
+        return;
+    }
+    c.Hbar = 0.25f * (w.c00 + w.c10 + w.c01 + w.c11);
+    c.HE = 0.5f * (w.c10 + w.c11); c.HW = 0.5f * (w.c00 + w.c01);
+    c.HN = 0.5f * (w.c01 + w.c11); c.HS = 0.5f * (w.c00 + w.c10);
+    c.f = w.f;
+    __sincosf(w.th, &c.st, &c.ct);
+    c.eta = w.q0; c.hu = w.q1; c.hv = w.q2;
+    if (STAGE == 2) { c.eta += w.d0; c.hu += w.d1; c.hv += w.d2; }
     make_prim(c, a.kappa, a.half_inv_kappa);
 }
 
@@ -139,13 +190,13 @@ __device__ __forceinline__ Face<float> shfl_dn_face(const Face<float> &F) {
 
 // Advance the device clock after the last block of stage 2 (see
 // clock_update in swe_kernels.cu).
-__device__ void finish_step(const StageArgs<float> &a, float block_speed) {
+__device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks) {
     __shared__ unsigned int last;
     if (threadIdx.x == 0) {
         atomicMax(&a.ctl->speed32, __float_as_uint(block_speed));
         __threadfence();
         unsigned int prev = atomicAdd(&a.ctl->blocks_done, 1u);
-        last = (prev == (unsigned int)a.nblocks - 1u);
+        last = (prev == (unsigned int)nblocks - 1u);
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
@@ -159,194 +210,311 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed) {
 
 }  // namespace
 
-template <int STAGE, bool KAHAN>
-__global__ void __launch_bounds__(kWarps * 32, 4) stage_fast_kernel(StageArgs<float> a, int rows) {
+// Per-warp constants of one strip.
+struct StripCtx {
+    int lane, i, j0, j1, par;
+    bool out_lane, frs_tile, wind_on, wind_uni;
+    float dt, taux, tauy, rho_ratio;
+};
+
+// The sliding window carried from row to row.
+struct Window {
+    RowCell A, B;                  // rows r-2 and r-1
+    float acc1[3], acc2[3];        // x-part of rows r-1 and r-2 (+ bed term in y)
+    float S1, S2;                  // drag rate of rows r-1 and r-2
+    Face<float> savedN;            // finished north face of row r-2
+    float Gprev[3];                // y-flux across the south face of row r-2
+    float speed;                   // running CFL maximum (stage 2)
+};
+
+// One row of the march: the x-part of row r (X), the y-reconstruction of
+// row r-1 (Y) and the flux across its south face (G), and the update of row
+// r-2 (OUT); the flags are warp-uniform. This body is instantiated once per
+// kernel on purpose: every cell then runs the same machine code wherever it
+// sits in a strip, so results do not depend on the tiling (bit for bit,
+// which the batch tests check). Land cells compute harmless values that
+// selects discard.
+template <int STAGE>
+__device__ __forceinline__ void march_row(const StageArgs<float> &a, const StripCtx &k, int r,
+                                          const Cell<float> &c, Window &w, const bool KAHAN,
+                                          const bool X, const bool Y, const bool G, const bool OUT) {
+    const float g = a.g, kappa = a.kappa, hik = a.half_inv_kappa;
+    float acc0[3] = {0.f, 0.f, 0.f}, S0 = 0.f;
+
+    // ---- x: reconstruction, fluxes and cell sources of row r
+    if (X) {
+        Cell<float> L, R;
+        L.land = __shfl_up_sync(0xffffffffu, c.land, 1);
+        L.eta = shfl_up1(c.eta); L.hu = shfl_up1(c.hu); L.hv = shfl_up1(c.hv);
+        L.fvx = shfl_up1(c.fvx);
+        R.land = __shfl_down_sync(0xffffffffu, c.land, 1);
+        R.eta = shfl_dn1(c.eta); R.hu = shfl_dn1(c.hu); R.hv = shfl_dn1(c.hv);
+        R.fvx = shfl_dn1(c.fvx);
+        Face<float> pE, pW;
+        reconstruct<float, 0>(L, c, R, a.kx, a.tm, pE, pW);
+        const float etaE = pE.eta, etaW = pW.eta;
+        finish_face(pE, g, kappa, hik);
+        finish_face(pW, g, kappa, hik);
+        // east face of this lane: (own E face | west face of lane + 1)
+        Face<float> nW = shfl_dn_face(pW);
+        const float HWr = shfl_dn1(c.HW);
+        Face<float> lf = c.land ? mirror<float, 0>(nW) : pE;
+        Face<float> rf = R.land ? mirror<float, 0>(pE) : nW;
+        float Fe[3];
+        cu_flux<float, 0>(lf, rf, c.land ? HWr : c.HE, g, Fe);
+        const bool none = c.land && R.land;
+        Fe[0] = none ? 0.f : Fe[0]; Fe[1] = none ? 0.f : Fe[1]; Fe[2] = none ? 0.f : Fe[2];
+        float Fw[3];
+        Fw[0] = shfl_up1(Fe[0]); Fw[1] = shfl_up1(Fe[1]); Fw[2] = shfl_up1(Fe[2]);
+        acc0[0] = -(Fe[0] - Fw[0]) * a.inv_dx;
+        acc0[1] = -(Fe[1] - Fw[1]) * a.inv_dx + g * 0.5f * (etaE + etaW) * (c.HE - c.HW) * a.inv_dx;
+        acc0[2] = -(Fe[2] - Fw[2]) * a.inv_dx;
+        // Coriolis with the north vector (Section 3.7) and wind stress
+        float hue = c.ct * c.hu - c.st * c.hv;
+        float hvn = c.st * c.hu + c.ct * c.hv;
+        acc0[1] += c.f * (c.ct * hvn - c.st * hue);
+        acc0[2] += c.f * (-c.st * hvn - c.ct * hue);
+        if (k.wind_on) {
+            if (k.wind_uni) {
+                acc0[1] += k.taux;
+                acc0[2] += k.tauy;
+            } else {
+                float tx, ty;
+                wind_at(a, k.i < 0 ? 0 : (k.i >= a.nx ? a.nx - 1 : k.i), r, STAGE - 1, k.rho_ratio, tx, ty);
+                acc0[1] += tx;
+                acc0[2] += ty;
+            }
+        }
+        S0 = c.land ? 0.f : a.cd * sqrtf(c.u * c.u + c.v * c.v) / fabsf(c.hs);
+    }
+
+    // ---- y: reconstruction of row r-1, flux across its south face
+    float Gcur[3] = {0.f, 0.f, 0.f};
+    if (Y) {
+        Cell<float> cA = as_cell(w.A), cB = as_cell(w.B), cC;
+        cC.land = c.land; cC.eta = c.eta; cC.hu = c.hu; cC.hv = c.hv; cC.fuy = c.fuy;
+        Face<float> pN, pS;
+        reconstruct<float, 1>(cA, cB, cC, a.ky, a.tm, pN, pS);
+        const float etaN = pN.eta, etaS = pS.eta;
+        finish_face(pN, g, kappa, hik);
+        finish_face(pS, g, kappa, hik);
+        if (G) {
+            // face between rows r-2 (A, north face savedN) and r-1 (B)
+            Face<float> lf = w.A.land ? mirror<float, 1>(pS) : w.savedN;
+            Face<float> rf = w.B.land ? mirror<float, 1>(w.savedN) : pS;
+            cu_flux<float, 1>(lf, rf, w.B.land ? w.A.HN : w.B.HS, g, Gcur);
+            const bool none = w.A.land && w.B.land;
+            Gcur[0] = none ? 0.f : Gcur[0]; Gcur[1] = none ? 0.f : Gcur[1]; Gcur[2] = none ? 0.f : Gcur[2];
+        }
+        // bed term of row r-1 in y (it is an output row whenever G and r-1 < j1)
+        if (G && r - 1 < k.j1) w.acc1[2] += g * 0.5f * (etaN + etaS) * (w.B.HN - w.B.HS) * a.inv_dy;
+        w.savedN = pN;
+    }
+
+    // ---- output row r-2
+    if (OUT) {
+        const int ro = r - 2;
+        const float m0 = w.acc2[0] - (Gcur[0] - w.Gprev[0]) * a.inv_dy;
+        const float m1 = w.acc2[1] - (Gcur[1] - w.Gprev[1]) * a.inv_dy;
+        const float m2 = w.acc2[2] - (Gcur[2] - w.Gprev[2]) * a.inv_dy;
+        const bool write = k.out_lane && !w.A.land;
+        const int s = ro * (int)a.pitch + k.i;
+        const float dt = k.dt, S2 = w.S2;
+        if (STAGE == 1) {
+            float den = 1.f / (1.f + dt * S2);
+            if (write) {
+                a.d1[0][s] = dt * m0;
+                a.d1[1][s] = (dt * m1 - dt * S2 * w.A.hu) * den;
+                a.d1[2][s] = (dt * m2 - dt * S2 * w.A.hv) * den;
+            }
+        } else if (write) {
+            const int par = k.par;
+            float q0 = a.q[par][0][s], q1 = a.q[par][1][s], q2 = a.q[par][2][s];
+            float D0 = a.d1[0][s], D1 = a.d1[1][s], D2 = a.d1[2][s];
+            float den = 1.f / (1.f + 0.5f * dt * S2);
+            float de0 = 0.5f * (D0 + dt * m0);
+            float de1 = 0.5f * (D1 + dt * m1 - dt * S2 * q1) * den;
+            float de2 = 0.5f * (D2 + dt * m2 - dt * S2 * q2) * den;
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+            if (KAHAN) {
+                c0 = a.comp[0][s]; c1 = a.comp[1][s]; c2 = a.comp[2][s];
+                kahan_add(q0, c0, de0); kahan_add(q1, c1, de1); kahan_add(q2, c2, de2);
+            } else {
+                q0 += de0; q1 += de1; q2 += de2;
+            }
+            // flow relaxation, eq:frs, nested edges in the order S, N, W, E
+            for (int e = 0; k.frs_tile && e < 4; e++) {
+                if (a.bc[e] != BC_NESTED) continue;
+                int d = e == EDGE_S ? ro : e == EDGE_N ? a.ny - 1 - ro : e == EDGE_W ? k.i : a.nx - 1 - k.i;
+                if (d >= a.frs_width) continue;
+                float al = a.frs_alpha_f[d];
+                float x0, x1, x2;
+                bnd_state_f(a, e, 0, e >= EDGE_W ? ro : k.i, 1, x0, x1, x2);
+                if (KAHAN) {
+                    kahan_add(q0, c0, al * (x0 - q0));
+                    kahan_add(q1, c1, al * (x1 - q1));
+                    kahan_add(q2, c2, al * (x2 - q2));
+                } else {
+                    q0 += al * (x0 - q0); q1 += al * (x1 - q1); q2 += al * (x2 - q2);
+                }
+            }
+            a.q[par ^ 1][0][s] = q0; a.q[par ^ 1][1][s] = q1; a.q[par ^ 1][2][s] = q2;
+            if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
+            if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + k.i);
+            w.speed = fmaxf(w.speed, cell_speed(a, q0, q1, q2, w.A.Hbar));
+        }
+    }
+
+    // ---- shift the window
+    w.Gprev[0] = Gcur[0]; w.Gprev[1] = Gcur[1]; w.Gprev[2] = Gcur[2];
+    w.acc2[0] = w.acc1[0]; w.acc2[1] = w.acc1[1]; w.acc2[2] = w.acc1[2]; w.S2 = w.S1;
+    w.acc1[0] = acc0[0]; w.acc1[1] = acc0[1]; w.acc1[2] = acc0[2]; w.S1 = S0;
+    w.A = w.B;
+    w.B = keep_row(c);
+}
+
+// One block of one domain: its kWarps warps take the warp items
+// blk*kWarps .. blk*kWarps+kWarps-1 of the domain, item = band*strips + strip,
+// each a strip of 28 output columns by `rows` rows. Numbering items
+// linearly (instead of giving a block a 2-D tile) leaves no idle warps at
+// the right edge and lets the tile height be chosen to fill whole waves.
+// `nblocks`: blocks of this domain in this launch (the last of them to
+// finish stage 2 advances the domain's clock).
+template <int STAGE>
+__device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, int rows, int strips,
+                                           int nblocks, const bool KAHAN) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int strip = blockIdx.x * kWarps + warp;
-    const int i = strip * kStrip - 2 + lane;
-    const int j0 = blockIdx.y * rows;
-    const int j1 = min(j0 + rows, a.ny);
-    const bool strip_live = strip * kStrip < a.nx;
-    const bool out_lane = lane >= 2 && lane < 2 + kStrip && i < a.nx;
-    const float g = a.g, kappa = a.kappa, hik = a.half_inv_kappa;
-    const float dt = (float)a.ctl->dt;
-    const float rho_ratio = (float)a.clk.rho_ratio;
-    float speed = 0.f;
-
-    // y-window: rows r-2 (A), r-1 (B), r (current); x-results of rows r-1, r-2
-    RowCell A, B;
-    A.land = B.land = true;
-    float acc1[3] = {0.f, 0.f, 0.f}, acc2[3] = {0.f, 0.f, 0.f};
-    float S1 = 0.f, S2 = 0.f;
-    Face<float> savedN;            // finished north face of row r-2
-    savedN.h = savedN.eta = savedN.hu = savedN.hv = savedN.u = savedN.v = savedN.c = 0.f;
-    float Gprev[3] = {0.f, 0.f, 0.f};
+    if (a.ctl->done) return;                       // forecast horizon reached (block-uniform)
+    const int bands = (a.ny + rows - 1) / rows;
+    const int item = blk * kWarps + warp;
+    const bool strip_live = item < strips * bands;
+    const int strip = strip_live ? item % strips : 0;
+    const int band = strip_live ? item / strips : 0;
+    StripCtx k;
+    k.lane = lane;
+    k.i = strip * kStrip - 2 + lane;
+    k.j0 = band * rows;
+    k.j1 = min(k.j0 + rows, a.ny);
+    k.par = a.ctl->parity;
+    k.out_lane = lane >= 2 && lane < 2 + kStrip && k.i < a.nx;
+    k.dt = (float)a.ctl->dt;
+    k.rho_ratio = (float)a.clk.rho_ratio;
+    k.wind_on = a.wind.n > 0;
+    k.wind_uni = a.clk.wind_uniform != 0;
+    k.taux = a.ctl->tau_f[STAGE - 1][0];
+    k.tauy = a.ctl->tau_f[STAGE - 1][1];
+    // does any cell of this warp's strip lie in a flow-relaxation zone?
+    {
+        const int c0 = strip * kStrip, c1 = c0 + kStrip, fw = a.frs_width;
+        k.frs_tile = STAGE == 2 &&
+            ((a.bc[EDGE_S] == BC_NESTED && k.j0 < fw) || (a.bc[EDGE_N] == BC_NESTED && k.j1 > a.ny - fw) ||
+             (a.bc[EDGE_W] == BC_NESTED && c0 < fw) || (a.bc[EDGE_E] == BC_NESTED && c1 > a.nx - fw));
+    }
+    Window w;
+    w.A.land = w.B.land = true;
+    w.A.eta = w.A.hu = w.A.hv = w.A.fuy = w.A.HN = w.A.HS = w.A.hbar = w.A.Hbar = 0.f;
+    w.B = w.A;
+    for (int q = 0; q < 3; q++) w.acc1[q] = w.acc2[q] = w.Gprev[q] = 0.f;
+    w.S1 = w.S2 = 0.f;
+    w.savedN.h = w.savedN.eta = w.savedN.hu = w.savedN.hv = w.savedN.u = w.savedN.v = w.savedN.c = 0.f;
+    w.speed = 0.f;
 
     if (strip_live) {
+        const int i = k.i, j0 = k.j0, j1 = k.j1, par = k.par;
+        RawCell<STAGE> cur, nxt;
+        fetch_cell<STAGE>(a, par, i, j0 - 2, cur);
         for (int r = j0 - 2; r <= j1 + 1; r++) {
+            if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, nxt);
             Cell<float> c;
-            load_cell_f<STAGE>(a, i, r, c);
-            float acc0[3] = {0.f, 0.f, 0.f}, S0 = 0.f;
-
-            // ---- x: reconstruction, fluxes and cell sources of row r
-            if (r >= j0 && r < j1) {
-                Cell<float> L, R;
-                L.land = __shfl_up_sync(0xffffffffu, c.land, 1);
-                L.eta = shfl_up1(c.eta); L.hu = shfl_up1(c.hu); L.hv = shfl_up1(c.hv);
-                L.fvx = shfl_up1(c.fvx);
-                R.land = __shfl_down_sync(0xffffffffu, c.land, 1);
-                R.eta = shfl_dn1(c.eta); R.hu = shfl_dn1(c.hu); R.hv = shfl_dn1(c.hv);
-                R.fvx = shfl_dn1(c.fvx);
-                Face<float> pE, pW;
-                pE.h = pE.eta = pE.hu = pE.hv = pW.h = pW.eta = pW.hu = pW.hv = 0.f;
-                if (!c.land) reconstruct<float, 0>(L, c, R, a.kx, a.tm, pE, pW);
-                const float etaE = pE.eta, etaW = pW.eta;
-                finish_face(pE, g, kappa, hik);
-                finish_face(pW, g, kappa, hik);
-                // east face of this lane: (own E face | west face of lane + 1)
-                Face<float> nW = shfl_dn_face(pW);
-                const float HWr = shfl_dn1(c.HW);
-                float Fe[3] = {0.f, 0.f, 0.f};
-                if (!(c.land && R.land)) {
-                    Face<float> lf = c.land ? mirror<float, 0>(nW) : pE;
-                    Face<float> rf = R.land ? mirror<float, 0>(pE) : nW;
-                    cu_flux<float, 0>(lf, rf, c.land ? HWr : c.HE, g, Fe);
-                }
-                float Fw[3];
-                Fw[0] = shfl_up1(Fe[0]); Fw[1] = shfl_up1(Fe[1]); Fw[2] = shfl_up1(Fe[2]);
-                acc0[0] = -(Fe[0] - Fw[0]) * a.inv_dx;
-                acc0[1] = -(Fe[1] - Fw[1]) * a.inv_dx + g * 0.5f * (etaE + etaW) * (c.HE - c.HW) * a.inv_dx;
-                acc0[2] = -(Fe[2] - Fw[2]) * a.inv_dx;
-                // Coriolis with the north vector (Section 3.7) and wind stress
-                float hue = c.ct * c.hu - c.st * c.hv;
-                float hvn = c.st * c.hu + c.ct * c.hv;
-                acc0[1] += c.f * (c.ct * hvn - c.st * hue);
-                acc0[2] += c.f * (-c.st * hvn - c.ct * hue);
-                if (a.wind.n > 0) {
-                    if (a.clk.wind_uniform) {
-                        acc0[1] += (float)a.ctl->tau[STAGE - 1][0];
-                        acc0[2] += (float)a.ctl->tau[STAGE - 1][1];
-                    } else {
-                        float tx, ty;
-                        wind_at(a, i < 0 ? 0 : (i >= a.nx ? a.nx - 1 : i), r, STAGE - 1, rho_ratio, tx, ty);
-                        acc0[1] += tx;
-                        acc0[2] += ty;
-                    }
-                }
-                S0 = c.land ? 0.f : a.cd * sqrtf(c.u * c.u + c.v * c.v) / fabsf(c.hs);
-            }
-
-            // ---- y: reconstruction of row r-1, flux across its south face
-            const int ry = r - 1;
-            float Gcur[3] = {0.f, 0.f, 0.f};
-            if (ry >= j0 - 1 && ry <= j1) {
-                Cell<float> cA = as_cell(A), cB = as_cell(B), cC;
-                cC.land = c.land; cC.eta = c.eta; cC.hu = c.hu; cC.hv = c.hv; cC.fuy = c.fuy;
-                Face<float> pN, pS;
-                pN.h = pN.eta = pN.hu = pN.hv = pS.h = pS.eta = pS.hu = pS.hv = 0.f;
-                if (!B.land) reconstruct<float, 1>(cA, cB, cC, a.ky, a.tm, pN, pS);
-                const float etaN = pN.eta, etaS = pS.eta;
-                finish_face(pN, g, kappa, hik);
-                finish_face(pS, g, kappa, hik);
-                if (ry >= j0) {
-                    // face between rows ry-1 (A, its north face savedN) and ry (B)
-                    if (!(A.land && B.land)) {
-                        Face<float> lf = A.land ? mirror<float, 1>(pS) : savedN;
-                        Face<float> rf = B.land ? mirror<float, 1>(savedN) : pS;
-                        cu_flux<float, 1>(lf, rf, B.land ? A.HN : B.HS, g, Gcur);
-                    }
-                }
-                if (ry >= j0 && ry < j1)
-                    acc1[2] += g * 0.5f * (etaN + etaS) * (B.HN - B.HS) * a.inv_dy;
-                savedN = pN;
-            }
-
-            // ---- output row r-2
-            const int ro = r - 2;
-            if (ro >= j0 && ro < j1 && out_lane && !A.land) {
-                float m0 = acc2[0] - (Gcur[0] - Gprev[0]) * a.inv_dy;
-                float m1 = acc2[1] - (Gcur[1] - Gprev[1]) * a.inv_dy;
-                float m2 = acc2[2] - (Gcur[2] - Gprev[2]) * a.inv_dy;
-                const long long s = (long long)ro * a.pitch + i;
-                if (STAGE == 1) {
-                    float den = 1.f / (1.f + dt * S2);
-                    a.d1[0][s] = dt * m0;
-                    a.d1[1][s] = (dt * m1 - dt * S2 * A.hu) * den;
-                    a.d1[2][s] = (dt * m2 - dt * S2 * A.hv) * den;
-                } else {
-                    float q0 = a.qin[0][s], q1 = a.qin[1][s], q2 = a.qin[2][s];
-                    float D0 = a.d1[0][s], D1 = a.d1[1][s], D2 = a.d1[2][s];
-                    float den = 1.f / (1.f + 0.5f * dt * S2);
-                    float de0 = 0.5f * (D0 + dt * m0);
-                    float de1 = 0.5f * (D1 + dt * m1 - dt * S2 * q1) * den;
-                    float de2 = 0.5f * (D2 + dt * m2 - dt * S2 * q2) * den;
-                    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
-                    if (KAHAN) {
-                        c0 = a.comp[0][s]; c1 = a.comp[1][s]; c2 = a.comp[2][s];
-                        kahan_add(q0, c0, de0); kahan_add(q1, c1, de1); kahan_add(q2, c2, de2);
-                    } else {
-                        q0 += de0; q1 += de1; q2 += de2;
-                    }
-                    // flow relaxation, eq:frs, nested edges in the order S, N, W, E
-                    for (int e = 0; e < 4; e++) {
-                        if (a.bc[e] != BC_NESTED) continue;
-                        int d = e == EDGE_S ? ro : e == EDGE_N ? a.ny - 1 - ro : e == EDGE_W ? i : a.nx - 1 - i;
-                        if (d >= a.frs_width) continue;
-                        float al = (float)a.frs_alpha[d];
-                        float x0, x1, x2;
-                        bnd_state_f(a, e, 0, e >= EDGE_W ? ro : i, 1, x0, x1, x2);
-                        if (KAHAN) {
-                            kahan_add(q0, c0, al * (x0 - q0));
-                            kahan_add(q1, c1, al * (x1 - q1));
-                            kahan_add(q2, c2, al * (x2 - q2));
-                        } else {
-                            q0 += al * (x0 - q0); q1 += al * (x1 - q1); q2 += al * (x2 - q2);
-                        }
-                    }
-                    a.qout[0][s] = q0; a.qout[1][s] = q1; a.qout[2][s] = q2;
-                    if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
-                    if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + i);
-                    speed = fmaxf(speed, cell_speed(a, q0, q1, q2, A.Hbar));
-                }
-            }
-
-            // ---- shift the window
-            Gprev[0] = Gcur[0]; Gprev[1] = Gcur[1]; Gprev[2] = Gcur[2];
-            acc2[0] = acc1[0]; acc2[1] = acc1[1]; acc2[2] = acc1[2]; S2 = S1;
-            acc1[0] = acc0[0]; acc1[1] = acc0[1]; acc1[2] = acc0[2]; S1 = S0;
-            A = B;
-            B = keep_row(c);
+            decode_cell<STAGE>(a, par, i, r, cur, c);
+            // which parts this row runs (warp-uniform): see march_row
+            march_row<STAGE>(a, k, r, c, w, KAHAN, r >= j0 && r < j1, r >= j0, r >= j0 + 1, r >= j0 + 2);
+            cur = nxt;
         }
     }
 
     if (STAGE == 2) {
         __shared__ float sh[kWarps];
+        float speed = w.speed;
         for (int o = 16; o > 0; o >>= 1) speed = fmaxf(speed, __shfl_xor_sync(0xffffffffu, speed, o));
         if (lane == 0) sh[warp] = speed;
         __syncthreads();
         float bs = 0.f;
         if (threadIdx.x == 0)
-            for (int w = 0; w < kWarps; w++) bs = fmaxf(bs, sh[w]);
-        finish_step(a, bs);
+            for (int q = 0; q < kWarps; q++) bs = fmaxf(bs, sh[q]);
+        finish_step(a, bs, nblocks);
+    }
+}
+
+// Persistent batch kernel: each block walks the tile table of all domains
+// (tile t belongs to the domain d with tile_start[d] <= t < tile_start[d+1]).
+// The table lives in device memory, so a captured graph of this kernel stays
+// valid when domains are added, removed or retiled.
+template <int STAGE>
+__global__ void __launch_bounds__(kWarps * 32, SWE_MIN_BLOCKS) stage_batch_kernel(const BatchTable tab) {
+    // the domain's arguments, staged once per block in shared memory (they
+    // are read uniformly by every thread; the table itself is in global memory)
+    __shared__ StageArgs<float> sa;
+    const int n_dom = *tab.n_domains;
+    const int total = n_dom > 0 ? tab.tile_start[n_dom] : 0;
+    int have = -1;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n_dom;                 // tile_start[lo] <= t < tile_start[hi]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (tab.tile_start[mid] <= t) lo = mid; else hi = mid;
+        }
+        const int d = lo;
+        if (d != have) {
+            const int *src = reinterpret_cast<const int *>(tab.args + d);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x)
+                dst[k] = src[k];
+            __syncthreads();
+            have = d;
+        }
+        const int ntiles = tab.tile_start[d + 1] - tab.tile_start[d];
+        stage_tile<STAGE>(sa, t - tab.tile_start[d], tab.rows[d], tab.grid_x[d], ntiles,
+                          sa.comp[0] != nullptr);
+        __syncthreads();                        // shared scratch reused by the next tile
     }
 }
 
 // ---------------------------------------------------------------------------
 // launch configuration
 
-int fast_rows(int nx, int ny) {
-    // enough warps to fill 152 SMs at ~16 resident warps each before growing
-    // the strips (halo rows cost 4 loads and 2 reconstructions per strip)
-    long long strips = (nx + kStrip - 1) / kStrip;
-    int rows = 64;
-    while (rows > 8 && strips * ((ny + rows - 1) / rows) < 152LL * 16) rows >>= 1;
-    return rows;
+static int warp_slots() {
+    static int slots = 0;
+    if (!slots) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<2>, kWarps * 32, 0);
+        slots = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4) * kWarps;
+    }
+    return slots;
 }
 
-dim3 fast_grid(int nx, int ny, int rows) {
-    int strips = (nx + kStrip - 1) / kStrip;
-    return dim3((strips + kWarps - 1) / kWarps, (ny + rows - 1) / rows);
+int fast_rows(int nx, int ny) {
+    // Score each tile height: the fraction of the last wave that is filled
+    // (warp items / whole waves of resident warps) times the share of
+    // useful rows (a halo row costs about a third of an output row: its
+    // loads, primitives and a y-reconstruction).
+    if (SWE_FORCE_ROWS > 0) return SWE_FORCE_ROWS;
+    const long long strips = (nx + kStrip - 1) / kStrip;
+    const double slots = warp_slots();
+    int best = 8;
+    double best_score = -1.0;
+    for (int rows = 8; rows <= 128; rows++) {
+        long long items = strips * ((ny + rows - 1) / rows);
+        double waves = (double)items / slots;
+        double fill = waves / (waves <= 1.0 ? 1.0 : (double)(long long)(waves + 0.999999));
+        double useful = (double)rows / (rows + 4.0 / 3.0);
+        double score = fill * useful;
+        if (score > best_score + 1e-9) { best_score = score; best = rows; }
+    }
+    return best;
 }
 
 int fast_step_parts() { return 2; }
@@ -356,15 +524,27 @@ const char *fast_part_name(int part) {
     return part >= 0 && part < 2 ? names[part] : "";
 }
 
-cudaError_t launch_step_fast_part(const StageArgs<float> &a0, cudaStream_t st, int part, bool kahan) {
-    StageArgs<float> a = a0;
-    int rows = fast_rows(a.nx, a.ny);
-    dim3 g = fast_grid(a.nx, a.ny, rows);
-    a.nblocks = (int)(g.x * g.y);
+// Blocks (of kWarps warp items) a domain needs; *strips_out: strips per row.
+int fast_tiles(int nx, int ny, int rows, int *strips_out) {
+    int strips = (nx + kStrip - 1) / kStrip;
+    long long items = (long long)strips * ((ny + rows - 1) / rows);
+    if (strips_out) *strips_out = strips;
+    return (int)((items + kWarps - 1) / kWarps);
+}
+
+int batch_grid_blocks() {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<2>, kWarps * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st) {
     dim3 b(kWarps * 32);
-    if (part == 0) stage_fast_kernel<1, false><<<g, b, 0, st>>>(a, rows);
-    else if (kahan) stage_fast_kernel<2, true><<<g, b, 0, st>>>(a, rows);
-    else stage_fast_kernel<2, false><<<g, b, 0, st>>>(a, rows);
+    if (stage == 1) stage_batch_kernel<1><<<blocks, b, 0, st>>>(tab);
+    else stage_batch_kernel<2><<<blocks, b, 0, st>>>(tab);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libswe.so")
+# SWE_LIBRARY may point at another build of the same library (tuning builds)
+LIB_PATH = os.environ.get("SWE_LIBRARY") or os.path.join(_HERE, "_build", "libswe.so")
 
 F32, F32_KAHAN, F64 = 0, 1, 2
 PRECISIONS = {"f32": F32, "f32_kahan": F32_KAHAN, "f64": F64}
@@ -52,7 +53,8 @@ class DomainDesc(C.Structure):
 class Info(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("step", C.c_longlong),
                 ("error", C.c_int), ("error_cell", C.c_int), ("error_step", C.c_longlong),
-                ("max_speed", C.c_double), ("launches", C.c_longlong)]
+                ("max_speed", C.c_double), ("launches", C.c_longlong),
+                ("done", C.c_int), ("t_end", C.c_double)]
 
 
 _lib = None
@@ -72,6 +74,7 @@ SIGNATURES = {
     "swe_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                   C.c_int, C.c_int]),
     "swe_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "swe_set_end_time": (C.c_int, [C.c_void_p, C.c_double]),
     "swe_launches_per_step": (C.c_int, [C.c_void_p]),
     "swe_launch_name": (C.c_char_p, [C.c_void_p, C.c_int]),
     "swe_step_profiled": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -81,6 +84,18 @@ SIGNATURES = {
     "swe_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "swe_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "swe_destroy_domain": (C.c_int, [C.c_void_p]),
+    "swe_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "swe_batch_add": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "swe_batch_remove": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "swe_batch_size": (C.c_int, [C.c_void_p]),
+    "swe_batch_set_rows": (C.c_int, [C.c_void_p, C.c_int]),
+    "swe_batch_rows": (C.c_int, [C.c_void_p]),
+    "swe_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "swe_batch_step_serial": (C.c_int, [C.c_void_p, C.c_int]),
+    "swe_batch_sync": (C.c_int, [C.c_void_p]),
+    "swe_batch_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "swe_batch_launches": (C.c_longlong, [C.c_void_p]),
+    "swe_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -199,6 +214,9 @@ class Domain:
     def step(self, n: int):
         _check(self._L.swe_step(self.h, int(n)), "swe_step")
 
+    def set_end_time(self, t_end: float):
+        _check(self._L.swe_set_end_time(self.h, float(t_end)), "swe_set_end_time")
+
     def launches_per_step(self) -> int:
         return self._L.swe_launches_per_step(self.h)
 
@@ -248,6 +266,69 @@ class Domain:
     def close(self):
         if getattr(self, "h", None):
             self._L.swe_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many FP32 domains advanced by one persistent launch per stage."""
+
+    def __init__(self, stream: int = 0, max_domains: int = 4096):
+        self._L = load()
+        h = C.c_void_p()
+        _check(self._L.swe_batch_create(C.c_void_p(stream), int(max_domains), C.byref(h)),
+               "swe_batch_create")
+        self.h = h
+        self.domains = []
+
+    def add(self, dom: "Domain"):
+        _check(self._L.swe_batch_add(self.h, dom.h), "swe_batch_add")
+        self.domains.append(dom)
+
+    def remove(self, dom: "Domain"):
+        _check(self._L.swe_batch_remove(self.h, dom.h), "swe_batch_remove")
+        self.domains.remove(dom)
+
+    def set_rows(self, rows: int):
+        _check(self._L.swe_batch_set_rows(self.h, int(rows)), "swe_batch_set_rows")
+
+    def rows(self) -> int:
+        return self._L.swe_batch_rows(self.h)
+
+    def step(self, n: int):
+        _check(self._L.swe_batch_step(self.h, int(n)), "swe_batch_step")
+
+    def step_serial(self, n: int):
+        _check(self._L.swe_batch_step_serial(self.h, int(n)), "swe_batch_step_serial")
+
+    def sync(self):
+        _check(self._L.swe_batch_sync(self.h), "swe_batch_sync")
+
+    def poll(self):
+        n = len(self.domains)
+        done = np.zeros(max(n, 1), dtype=np.int32)
+        t = np.zeros(max(n, 1), dtype=np.float64)
+        _check(self._L.swe_batch_poll(self.h, done.ctypes.data, t.ctypes.data, max(n, 1)),
+               "swe_batch_poll")
+        return done[:n].astype(bool), t[:n]
+
+    def launches(self) -> int:
+        return self._L.swe_batch_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.swe_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -121,3 +121,35 @@ def rel(a, b):
     b = np.asarray(b, dtype=np.float64)
     s = max(np.abs(a).max(), np.abs(b).max(), 1e-300)
     return float(np.abs(a - b).max() / s)
+
+
+def max_filter(a, r):
+    """(2r+1)^2 maximum filter (periodic at the edges, fine for masks that
+    stay away from them)."""
+    out = a.copy()
+    for dj in range(-r, r + 1):
+        for di in range(-r, r + 1):
+            out = np.maximum(out, np.roll(np.roll(a, dj, axis=0), di, axis=1))
+    return out
+
+
+def ulp_perturbed(wl, seed=1):
+    """The workload with eta and the wet corner depths moved by one float32
+    ulp in random directions (FP64 values)."""
+    from paper_1912_02457_gb300 import synth
+    rng = np.random.default_rng(seed)
+    w2 = wl.copy()
+    w2.eta = wl.eta.astype(np.float64) * (1 + 6e-8 * rng.choice([-1, 1], wl.eta.shape))
+    Hm = wl.H.astype(np.float64)
+    w2.H = np.where(wl.H == synth.LAND, Hm, Hm * (1 + 6e-8 * rng.choice([-1, 1], Hm.shape)))
+    return w2.astype(np.float64)
+
+
+def front_set(wl, eta_end, depth=0.01, radius=3):
+    """Wet cells dry (hbar <= depth) at the start or at the end, dilated."""
+    from paper_1912_02457_gb300 import synth
+    Hm = np.where(wl.H == synth.LAND, np.nan, wl.H.astype(np.float64))
+    Hbar = 0.25 * (Hm[:-1, :-1] + Hm[1:, :-1] + Hm[:-1, 1:] + Hm[1:, 1:])
+    land = wl.land_cells()
+    dry = (((wl.eta.astype(np.float64) + Hbar) <= depth) | ((eta_end + Hbar) <= depth)) & ~land
+    return max_filter(dry.astype(np.int8), radius).astype(bool) & ~land

@@ -1,0 +1,28 @@
+"""The wet-dry front is where the scheme is ill-conditioned (CPU only).
+
+Whether a dry cell wets on a given step is a threshold decision (the face
+depths of eq:hE and the re-sloping of eq:KxE_adjust). Perturbing the FP64
+oracle at float32 level (its inputs moved by one ulp, or its state stored in
+float32 after every stage) moves its solution by more than 1e-4 m on front
+cells after 1000 steps and by far less everywhere else. This is why the GPU
+parity tests hold float32 results to 1e-4 m off the fronts and bound them
+separately on the fronts."""
+import numpy as np
+
+from paper_1912_02457_gb300 import synth
+from tests import helpers
+
+
+def test_front_sensitivity_is_confined_to_fronts(oracle_mod):
+    wl = synth.coastal(96, 80, seed_config=92, member=1, dtype=np.float32)
+    ref = oracle_mod.Oracle(wl).run(1000)
+    ulp = oracle_mod.Oracle(helpers.ulp_perturbed(wl)).run(1000)
+    f32 = oracle_mod.Oracle(wl, round_state_f32=True).run(1000)
+    front = helpers.front_set(wl, ref[0])
+    wet = ~wl.land_cells()
+    d_ulp = np.abs(ulp[0] - ref[0])
+    d_f32 = np.abs(f32[0] - ref[0])
+    assert front.sum() < 0.25 * wet.sum()
+    assert d_ulp[wet & ~front].max() < 1e-6
+    assert d_f32[wet & ~front].max() < 5e-5
+    assert max(d_ulp[front].max(), d_f32[front].max()) > 1e-4
