@@ -245,6 +245,33 @@ int swe_batch_poll(swe_batch_handle b, int *done, double *t, int capacity);
 long long swe_batch_launches(swe_batch_handle b);
 int swe_batch_destroy(swe_batch_handle b);
 
+/* ---- diagnostics for callers that cannot allocate ----------------------
+ * The paper has no counterpart to this function; it is a service of this
+ * library. It computes what swe_diagnostics computes (FP64 mass and
+ * energy over the water cells) from caller-owned FP32 device planes, and
+ * allocates nothing, for callers that cannot allocate device memory where
+ * they need the numbers: code running while a stream is captured into a
+ * CUDA graph (cudaMalloc is not allowed there), code inside a framework
+ * that owns every device buffer through its own pool, real-time loops in
+ * which an allocation may block.
+ *   eta, hu, hv: device planes, ny rows of `pitch` floats (pitch >= nx);
+ *   H: device corner depths, ny+1 rows of `cpitch` floats (cpitch >= nx+1),
+ *      SWE_LAND at land corners; dx, dy, g, kappa as in swe_params;
+ *   out: device pointer to 2 doubles, written stream-ordered on `stream`.
+ * Scratch: per-row partial sums in a fixed device array of
+ * SWE_NOALLOC_MAX_ROWS rows (256 KiB) that every GPU loading the library
+ * keeps until the process exits; ny > SWE_NOALLOC_MAX_ROWS is rejected with
+ * SWE_ERR_INVALID_ARG. The first call on each device looks the array's
+ * device address up (cudaGetSymbolAddress), so make that first call before
+ * any stream capture. Every call writes the partials it reads, so nothing
+ * carries over between calls, but all calls share the one array: calls
+ * that overlap on the GPU (other streams, other host threads) race, so
+ * order them on one stream. */
+#define SWE_NOALLOC_MAX_ROWS 16384
+int swe_diagnostics_noalloc(const float *eta, const float *hu, const float *hv, const float *H,
+                            int nx, int ny, long long pitch, long long cpitch, double dx,
+                            double dy, double g, double kappa, double *out, void *stream);
+
 /* The last CUDA error string recorded by this thread, or "". */
 const char *swe_last_cuda_error(void);
 const char *swe_status_string(int status);

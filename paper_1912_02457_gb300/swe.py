@@ -96,7 +96,24 @@ SIGNATURES = {
     "swe_batch_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "swe_batch_launches": (C.c_longlong, [C.c_void_p]),
     "swe_batch_destroy": (C.c_int, [C.c_void_p]),
+    "swe_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_int, C.c_int, C.c_longlong, C.c_longlong,
+                                          C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_void_p, C.c_void_p]),
 }
+
+NOALLOC_MAX_ROWS = 16384
+
+
+def diagnostics_noalloc(eta_ptr, hu_ptr, hv_ptr, H_ptr, nx, ny, pitch, cpitch, dx, dy,
+                        out_ptr, g=9.81, kappa=1e-2, stream=0):
+    """Mass and energy of caller-owned FP32 device planes into a caller-owned
+    device buffer of 2 doubles, without any device allocation (see swe.h)."""
+    _check(load().swe_diagnostics_noalloc(C.c_void_p(eta_ptr), C.c_void_p(hu_ptr),
+                                          C.c_void_p(hv_ptr), C.c_void_p(H_ptr), int(nx), int(ny),
+                                          int(pitch), int(cpitch), float(dx), float(dy), float(g),
+                                          float(kappa), C.c_void_p(out_ptr), C.c_void_p(stream)),
+           "swe_diagnostics_noalloc")
 
 
 def load(path: str = LIB_PATH):
