@@ -363,6 +363,111 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# secondary workloads (one JSON line each; the default line is the step above)
+
+def _timed_steps(torch, dom_or_batch, n, stream, method="step"):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    getattr(dom_or_batch, method)(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_sweep(args):
+    """Single domains of the coastal recipe at growing sizes (inputs larger
+    than L2 from 2048^2 on): cell-updates/s of back-to-back graph steps."""
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+    build.build()
+    swe.load()
+    stream = torch.cuda.Stream()
+    out = []
+    for nx, ny in synth.SWEEP_SIZES:
+        wl = synth.coastal(nx, ny, dtype=np.float32)
+        with swe.Domain(wl, args.precision, stream=stream.cuda_stream) as d:
+            d.step(args.warmup)
+            n = max(32, min(args.steps, int(4e10 // (nx * ny))))
+            el = _timed_steps(torch, d, n, stream)
+            ms = d.step_profiled(8).mean(axis=0)
+            ab = algorithmic_bytes(wl, args.precision)
+            out.append({"nx": nx, "ny": ny, "steps": n, "cell_updates_per_s": float(nx * ny * n / el),
+                        "stage_ms": {"stage1": float(ms[0]), "stage2": float(ms[1])},
+                        "stage2_hbm_frac": float(ab["stage2"] / (float(ms[1]) * 1e-3) / 1e9
+                                                 / measured_hbm_peak()[0])})
+        del wl
+    print(json.dumps({"metric": METRIC, "workload": "size sweep (coastal recipe)",
+                      "unit": UNIT, "precision": args.precision, "results": out}), flush=True)
+
+
+def run_ensemble(args):
+    """64 domains of uneven sizes in one batch: one persistent launch per
+    stage (graph-captured, autotuned tiles) against launching the same
+    kernels domain after domain."""
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+    build.build()
+    swe.load()
+    stream = torch.cuda.Stream()
+    wls = synth.ensemble(args.domains)
+    cells = sum(w.nx * w.ny for w in wls)
+    doms = [swe.Domain(w, "f32_kahan", stream=stream.cuda_stream) for w in wls]
+    b = swe.Batch(stream=stream.cuda_stream)
+    for d in doms:
+        b.add(d)
+    b.step(32)                                   # autotune + warm-up
+    b.step_serial(4)
+    n = args.steps
+    t_batched = _timed_steps(torch, b, n, stream, "step")
+    t_serial = _timed_steps(torch, b, n, stream, "step_serial")
+    res = {"metric": METRIC, "workload": f"ensemble of {len(wls)} coastal domains "
+           "(256^2, 512x384, 1024^2, 2048x1024), FP32 + Kahan",
+           "unit": UNIT, "domains": len(wls), "cells": cells, "steps": n,
+           "batched_value": cells * n / t_batched, "serial_value": cells * n / t_serial,
+           "speedup_vs_one_by_one": t_serial / t_batched, "tile_rows": b.rows(),
+           "batched_ms_per_step": 1e3 * t_batched / n, "serial_ms_per_step": 1e3 * t_serial / n}
+    b.close()
+    for d in doms:
+        d.close()
+    print(json.dumps(res), flush=True)
+
+
+def run_serve(args):
+    """Poisson forecast requests (20/s, sides log-uniform 128-2048, horizons
+    1-24 h scaled by --horizon-scale) served by continuous batching under a
+    150 GB budget; inputs are generated before the clock starts."""
+    import torch
+    from paper_1912_02457_gb300 import build, serve, swe, synth
+    build.build()
+    swe.load()
+    stream = torch.cuda.Stream()
+    trace = synth.serving_trace(args.requests)
+    reqs = []
+    for r in trace:
+        wl = synth.coastal(r["side"], r["side"], seed_config=5, member=r["member"] + 1,
+                           dtype=np.float32, hours=int(np.ceil(r["horizon"] * args.horizon_scale / 3600)) + 1)
+        reqs.append(serve.Request(rid=r["member"], arrival=r["arrival"],
+                                  make_workload=(lambda w=wl: w),
+                                  horizon=r["horizon"] * args.horizon_scale,
+                                  nx=r["side"], ny=r["side"]))
+    backend = serve.GpuBackend(stream=stream.cuda_stream)
+    srv = serve.ForecastServer(backend, budget_bytes=150e9, round_steps=args.round_steps)
+    t0 = time.perf_counter()
+    srv.run(reqs)
+    wall = time.perf_counter() - t0
+    backend.shutdown()
+    st = serve.ForecastServer.stats(reqs, wall)
+    offered = sum(r.nx * r.ny * (r.horizon / 0.93) for r in reqs) / max(trace[-1]["arrival"], 1e-9)
+    st.update({"metric": METRIC, "workload": f"serving: {len(reqs)} Poisson requests at 20/s, "
+               f"horizons x{args.horizon_scale}", "unit": "s (latency), cell-updates/s",
+               "offered_cell_updates_per_s_est": offered, "peak_device_bytes": srv.peak_used,
+               "rounds": srv.rounds, "round_steps": args.round_steps})
+    print(json.dumps(st), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,11 +477,23 @@ def main():
     ap.add_argument("--precision", choices=("f32", "f32_kahan"), default="f32_kahan")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve"),
+                    default="coastal1024")
+    ap.add_argument("--domains", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--horizon-scale", type=float, default=1.0 / 12.0)
+    ap.add_argument("--round-steps", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

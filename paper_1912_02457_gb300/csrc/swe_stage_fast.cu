@@ -241,6 +241,20 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
     const float g = a.g, kappa = a.kappa, hik = a.half_inv_kappa;
     float acc0[3] = {0.f, 0.f, 0.f}, S0 = 0.f;
 
+    // the loads of the output row are issued first so that their latency
+    // hides behind the x and y work of this iteration
+    const bool write = OUT && k.out_lane && !w.A.land;
+    const int s_out = (r - 2) * (int)a.pitch + k.i;
+    float oq[3] = {0.f, 0.f, 0.f}, oD[3] = {0.f, 0.f, 0.f}, oc[3] = {0.f, 0.f, 0.f};
+    if (STAGE == 2 && write) {
+        for (int v = 0; v < 3; v++) {
+            oq[v] = __ldg(a.q[k.par][v] + s_out);
+            oD[v] = __ldg(a.d1[v] + s_out);
+        }
+        if (KAHAN)
+            for (int v = 0; v < 3; v++) oc[v] = a.comp[v][s_out];
+    }
+
     // ---- x: reconstruction, fluxes and cell sources of row r
     if (X) {
         Cell<float> L, R;
@@ -317,8 +331,7 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
         const float m0 = w.acc2[0] - (Gcur[0] - w.Gprev[0]) * a.inv_dy;
         const float m1 = w.acc2[1] - (Gcur[1] - w.Gprev[1]) * a.inv_dy;
         const float m2 = w.acc2[2] - (Gcur[2] - w.Gprev[2]) * a.inv_dy;
-        const bool write = k.out_lane && !w.A.land;
-        const int s = ro * (int)a.pitch + k.i;
+        const int s = s_out;
         const float dt = k.dt, S2 = w.S2;
         if (STAGE == 1) {
             float den = 1.f / (1.f + dt * S2);
@@ -329,15 +342,14 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
             }
         } else if (write) {
             const int par = k.par;
-            float q0 = a.q[par][0][s], q1 = a.q[par][1][s], q2 = a.q[par][2][s];
-            float D0 = a.d1[0][s], D1 = a.d1[1][s], D2 = a.d1[2][s];
+            float q0 = oq[0], q1 = oq[1], q2 = oq[2];
+            const float D0 = oD[0], D1 = oD[1], D2 = oD[2];
             float den = 1.f / (1.f + 0.5f * dt * S2);
             float de0 = 0.5f * (D0 + dt * m0);
             float de1 = 0.5f * (D1 + dt * m1 - dt * S2 * q1) * den;
             float de2 = 0.5f * (D2 + dt * m2 - dt * S2 * q2) * den;
-            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+            float c0 = oc[0], c1 = oc[1], c2 = oc[2];
             if (KAHAN) {
-                c0 = a.comp[0][s]; c1 = a.comp[1][s]; c2 = a.comp[2][s];
                 kahan_add(q0, c0, de0); kahan_add(q1, c1, de1); kahan_add(q2, c2, de2);
             } else {
                 q0 += de0; q1 += de1; q2 += de2;
