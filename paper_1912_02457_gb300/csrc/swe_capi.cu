@@ -53,6 +53,7 @@ struct swe_domain {
     void *H = nullptr, *f = nullptr, *th = nullptr;
     double f_const = 0, th_const = 0;
     StepCtl *ctl = nullptr;
+    float *edge = nullptr;             // external edge state, two time levels (fast path)
     float *bnd = nullptr;
     double *bnd_t = nullptr;
     int bnd_n = 0, bnd_n1 = 0, bnd_n2 = 0;
@@ -158,6 +159,7 @@ StageArgs<T> make_args(const swe_domain *d) {
         a.frs_alpha_f[k] = (float)a.frs_alpha[k];
     }
     a.ctl = d->ctl;
+    a.edge = d->edge;
     a.clk.courant = d->p.courant;
     a.clk.dt_fixed = d->p.dt_fixed;
     a.clk.dt_every = d->p.dt_update_every < 1 ? 1 : d->p.dt_update_every;
@@ -205,6 +207,8 @@ int init_clock(swe_domain *d, double t, double dt, long long step) {
     cudaError_t e;
     if (d->prec == SWE_F64) e = swe::launch_init_clock(make_args<double>(d), d->stream, t, dt, step);
     else e = swe::launch_init_clock(make_args<float>(d), d->stream, t, dt, step);
+    // the fast path reads the ghosts of the current time level from the edge buffer
+    if (e == cudaSuccess && d->fast()) e = swe::launch_edge_fill(make_args<float>(d), d->stream);
     return e == cudaSuccess ? SWE_OK : cuda_fail(e);
 }
 
@@ -212,6 +216,7 @@ int refresh_brackets(swe_domain *d) {
     cudaError_t e;
     if (d->prec == SWE_F64) e = swe::launch_refresh_brackets(make_args<double>(d), d->stream);
     else e = swe::launch_refresh_brackets(make_args<float>(d), d->stream);
+    if (e == cudaSuccess && d->fast()) e = swe::launch_edge_fill(make_args<float>(d), d->stream);
     return e == cudaSuccess ? SWE_OK : cuda_fail(e);
 }
 
@@ -251,6 +256,9 @@ int create_impl(const swe_domain_desc *dd, const swe_params *p, void *stream, sw
     d->th_const = dd->theta_const;
     if (!(d->ctl = (StepCtl *)d->dalloc(sizeof(StepCtl)))) return SWE_ERR_OOM;
     if (d->fast()) {
+        const size_t eb = (size_t)swe::edge_floats(d->nx, d->ny) * sizeof(float);
+        if (!(d->edge = (float *)d->dalloc(eb))) return SWE_ERR_OOM;
+        CK(cudaMemsetAsync(d->edge, 0, eb, d->stream));
         if (!(d->t_args = (swe::StageArgs<float> *)d->dalloc(sizeof(swe::StageArgs<float>))) ||
             !(d->t_start = (int *)d->dalloc(2 * sizeof(int))) || !(d->t_gx = (int *)d->dalloc(sizeof(int))) ||
             !(d->t_rows = (int *)d->dalloc(sizeof(int))) || !(d->t_n = (int *)d->dalloc(sizeof(int))))

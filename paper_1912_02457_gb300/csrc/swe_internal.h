@@ -74,6 +74,13 @@ struct StageArgs {
     float frs_alpha_f[kMaxFrs];   // the same weights rounded once for FP32 kernels
     StepCtl *ctl;
     ClockParams clk;
+    // FP32 fast path: the external state of Section 3.6 on the two ghost
+    // rings of every nested edge, one copy per time level (two levels,
+    // selected by the step parity); NULL on the other paths. A level holds
+    // 12 (nx + ny) floats: edge S at 0, N at 6 nx, W at 12 nx, E at
+    // 12 nx + 6 ny; within an edge of length n, value v of ring r at
+    // position k sits at (3 r + v) n + k.
+    float *edge;
 };
 
 // Device-resident tile table of a batch of FP32 domains (persistent kernel).

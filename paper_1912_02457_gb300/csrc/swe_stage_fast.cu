@@ -66,78 +66,91 @@ __device__ __forceinline__ void bnd_state_f(const StageArgs<float> &a, int e, in
     v0 = out[0]; v1 = out[1]; v2 = out[2];
 }
 
-// Cell (i, r) with its primitives; Q* = Q^n + D1 in stage 2. Outside a
-// wall the cell is land; outside a nested edge it is the ghost of
-// Section 3.6 (mirrored statics, external state).
-template <int STAGE>
-__device__ __forceinline__ void load_cell_f(const StageArgs<float> &a, int par, int i, int r, Cell<float> &c) {
-    const int nx = a.nx, ny = a.ny;
-    int si = i, sj = r, e = -1, row = 0;
-    const bool ox = i < 0 || i >= nx, oy = r < 0 || r >= ny;
-    c.land = true;
-    c.eta = c.hu = c.hv = c.Hbar = c.HE = c.HW = c.HN = c.HS = 0.f;
-    c.f = c.ct = c.st = c.hbar = c.hs = c.u = c.v = c.fvx = c.fuy = 0.f;
-    if (ox && oy) return;                           // ghost-ghost corner: unused
-    if (i < -2 || i > nx + 1) return;               // beyond the halo of the last strip
-    if (i < 0)        { e = EDGE_W; si = -i - 1;         row = -i - 1; }
-    else if (i >= nx) { e = EDGE_E; si = 2 * nx - 1 - i; row = i - nx; }
-    else if (r < 0)   { e = EDGE_S; sj = -r - 1;         row = -r - 1; }
-    else if (r >= ny) { e = EDGE_N; sj = 2 * ny - 1 - r; row = r - ny; }
-    if (e >= 0 && a.bc[e] == BC_WALL) return;
-    const long long cp = a.cpitch;
-    const float *H = a.H + (long long)sj * cp + si;
-    float c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];
-    if ((c00 == kLand) | (c10 == kLand) | (c01 == kLand) | (c11 == kLand)) return;
-    c.land = false;
-    c.Hbar = 0.25f * (c00 + c10 + c01 + c11);
-    float HE = 0.5f * (c10 + c11), HW = 0.5f * (c00 + c01);
-    float HN = 0.5f * (c01 + c11), HS = 0.5f * (c00 + c10);
-    if (e == EDGE_W || e == EDGE_E) { float t = HE; HE = HW; HW = t; }
-    if (e == EDGE_S || e == EDGE_N) { float t = HN; HN = HS; HS = t; }
-    c.HE = HE; c.HW = HW; c.HN = HN; c.HS = HS;
-    const long long s = (long long)sj * a.pitch + si;
-    c.f = a.f ? __ldg(a.f + s) : a.f_const;
-    float th = a.th ? __ldg(a.th + s) : a.th_const;
-    __sincosf(th, &c.st, &c.ct);
-    if (e < 0) {
-        c.eta = a.q[par][0][s]; c.hu = a.q[par][1][s]; c.hv = a.q[par][2][s];
-        if (STAGE == 2) { c.eta += a.d1[0][s]; c.hu += a.d1[1][s]; c.hv += a.d1[2][s]; }
-    } else {
-        int k = e >= EDGE_W ? r : i;
-        bnd_state_f(a, e, row, k, STAGE - 1, c.eta, c.hu, c.hv);
-    }
-    make_prim(c, a.kappa, a.half_inv_kappa);
+// Offset of edge e within one time level of the edge-state buffer.
+__device__ __forceinline__ int edge_base(int e, int nx, int ny) {
+    return e == EDGE_S ? 0 : e == EDGE_N ? 6 * nx : e == EDGE_W ? 12 * nx : 12 * nx + 6 * ny;
 }
 
-// Raw loads of one cell of the next row, issued one iteration ahead of use
-// so their latency hides behind the current row's arithmetic. `fast`: an
-// interior cell (ghosts and out-of-range cells take load_cell_f).
+// Evaluate the external state (bnd_state_f, stage brackets `stage`) on both
+// ghost rings of every nested edge into time level `slot` of the edge-state
+// buffer; entries idx, idx + stride, ... of the 4 (nx + ny) (edge, ring,
+// position) entries. Every later ghost or relaxation read of that time
+// level is one load of these values instead of a bracket and frame lookup.
+__device__ void edge_fill(const StageArgs<float> &a, int slot, int stage, int idx, int stride) {
+    if (!a.edge || a.bnd.n <= 0) return;
+    const int nx = a.nx, ny = a.ny;
+    const int total = 4 * (nx + ny);
+    float *L = a.edge + (long long)slot * 12 * (nx + ny);
+    for (; idx < total; idx += stride) {
+        int e, q = idx;
+        if (q < 2 * nx) e = EDGE_S;
+        else if ((q -= 2 * nx) < 2 * nx) e = EDGE_N;
+        else if ((q -= 2 * nx) < 2 * ny) e = EDGE_W;
+        else { q -= 2 * ny; e = EDGE_E; }
+        if (a.bc[e] != BC_NESTED) continue;
+        const int n = e < 2 ? nx : ny;
+        const int r = q / n, k = q - r * n;
+        float v0, v1, v2;
+        bnd_state_f(a, e, r, k, stage, v0, v1, v2);
+        float *o = L + edge_base(e, nx, ny) + 3 * r * n + k;
+        o[0] = v0; o[n] = v1; o[2 * n] = v2;
+    }
+}
+
+// Raw loads of one cell, issued one iteration ahead of use so their latency
+// hides behind the current row's arithmetic. Interior cells and the ghosts
+// of nested edges (Section 3.6: statics mirrored from the cells inside the
+// edge, external state from the edge-state buffer) take the same loads;
+// cells outside a wall, the ghost-ghost corners and lanes beyond the halo
+// of the last strip are land (all four corners LAND). Stage 2 adds the increment
+// D1 to interior cells; a ghost adds -0.0f, which leaves every value as it
+// is.
 template <int STAGE>
 struct RawCell {
-    bool fast;
     float c00, c10, c01, c11, f, th, q0, q1, q2, d0, d1, d2;
 };
 
 template <int STAGE>
 __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, int i, int r,
                                            RawCell<STAGE> &w) {
-    w.fast = (unsigned)i < (unsigned)a.nx && (unsigned)r < (unsigned)a.ny;
-    if (!w.fast) return;
+    const int nx = a.nx, ny = a.ny;
+    const bool ox = (unsigned)i >= (unsigned)nx, oy = (unsigned)r >= (unsigned)ny;
+    int si = i, sj = r, e = -1, ring = 0;
+    if (i < 0)        { e = EDGE_W; si = -i - 1;         ring = si; }
+    else if (i >= nx) { e = EDGE_E; si = 2 * nx - 1 - i; ring = i - nx; }
+    else if (r < 0)   { e = EDGE_S; sj = -r - 1;         ring = sj; }
+    else if (r >= ny) { e = EDGE_N; sj = 2 * ny - 1 - r; ring = r - ny; }
+    if ((ox && oy) || i < -2 || i > nx + 1 || (e >= 0 && a.bc[e] != BC_NESTED)) {
+        w.c00 = w.c10 = w.c01 = w.c11 = kLand;
+        return;
+    }
     // offsets fit in 32 bits (checked when the domain is created)
     const int cp = (int)a.cpitch;
-    const float *H = a.H + (r * cp + i);
+    const float *H = a.H + (sj * cp + si);
     w.c00 = __ldg(H); w.c10 = __ldg(H + 1); w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
-    const int s = r * (int)a.pitch + i;
+    const int s = sj * (int)a.pitch + si;
     w.f = a.f ? __ldg(a.f + s) : a.f_const;
     w.th = a.th ? __ldg(a.th + s) : a.th_const;
-    w.q0 = __ldg(a.q[par][0] + s); w.q1 = __ldg(a.q[par][1] + s); w.q2 = __ldg(a.q[par][2] + s);
-    if (STAGE == 2) { w.d0 = __ldg(a.d1[0] + s); w.d1 = __ldg(a.d1[1] + s); w.d2 = __ldg(a.d1[2] + s); }
+    // an interior cell reads the state planes; a ghost reads its edge's values,
+    // stage 1 at the time level of Q^n (slot par), stage 2 at the next one
+    const float *p0 = a.q[par][0] + s, *p1 = a.q[par][1] + s, *p2 = a.q[par][2] + s;
+    if (e >= 0) {
+        const int n = e < 2 ? nx : ny;
+        const int slot = STAGE == 1 ? par : par ^ 1;
+        p0 = a.edge + slot * 12 * (nx + ny) + edge_base(e, nx, ny) + 3 * ring * n + (e >= EDGE_W ? r : i);
+        p1 = p0 + n;
+        p2 = p1 + n;
+    }
+    w.q0 = __ldg(p0); w.q1 = __ldg(p1); w.q2 = __ldg(p2);
+    if (STAGE == 2) {
+        w.d0 = w.d1 = w.d2 = -0.0f;
+        if (e < 0) { w.d0 = __ldg(a.d1[0] + s); w.d1 = __ldg(a.d1[1] + s); w.d2 = __ldg(a.d1[2] + s); }
+    }
 }
 
 template <int STAGE>
-__device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int par, int i, int r,
+__device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int i, int r,
                                             const RawCell<STAGE> &w, Cell<float> &c) {
-    if (!w.fast) { load_cell_f<STAGE>(a, par, i, r, c); return; }
     c.land = (w.c00 == kLand) | (w.c10 == kLand) | (w.c01 == kLand) | (w.c11 == kLand);
     if (c.land) {
         c.eta = c.hu = c.hv = c.Hbar = c.HE = c.HW = c.HN = c.HS = 0.f;
@@ -145,8 +158,12 @@ __device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int par, 
         return;
     }
     c.Hbar = 0.25f * (w.c00 + w.c10 + w.c01 + w.c11);
-    c.HE = 0.5f * (w.c10 + w.c11); c.HW = 0.5f * (w.c00 + w.c01);
-    c.HN = 0.5f * (w.c01 + w.c11); c.HS = 0.5f * (w.c00 + w.c10);
+    float HE = 0.5f * (w.c10 + w.c11), HW = 0.5f * (w.c00 + w.c01);
+    float HN = 0.5f * (w.c01 + w.c11), HS = 0.5f * (w.c00 + w.c10);
+    // a ghost's statics are mirrored across its edge
+    const bool swap_x = (unsigned)i >= (unsigned)a.nx, swap_y = (unsigned)r >= (unsigned)a.ny;
+    c.HE = swap_x ? HW : HE; c.HW = swap_x ? HE : HW;
+    c.HN = swap_y ? HS : HN; c.HS = swap_y ? HN : HS;
     c.f = w.f;
     __sincosf(w.th, &c.st, &c.ct);
     c.eta = w.q0; c.hu = w.q1; c.hv = w.q2;
@@ -360,8 +377,11 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
                 int d = e == EDGE_S ? ro : e == EDGE_N ? a.ny - 1 - ro : e == EDGE_W ? k.i : a.nx - 1 - k.i;
                 if (d >= a.frs_width) continue;
                 float al = a.frs_alpha_f[d];
-                float x0, x1, x2;
-                bnd_state_f(a, e, 0, e >= EDGE_W ? ro : k.i, 1, x0, x1, x2);
+                // external state at the new time level, ring 0
+                const int n = e < 2 ? a.nx : a.ny;
+                const float *E = a.edge + (par ^ 1) * 12 * (a.nx + a.ny) + edge_base(e, a.nx, a.ny) +
+                                 (e >= EDGE_W ? ro : k.i);
+                const float x0 = __ldg(E), x1 = __ldg(E + n), x2 = __ldg(E + 2 * n);
                 if (KAHAN) {
                     kahan_add(q0, c0, al * (x0 - q0));
                     kahan_add(q1, c1, al * (x1 - q1));
@@ -409,6 +429,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     k.j0 = band * rows;
     k.j1 = min(k.j0 + rows, a.ny);
     k.par = a.ctl->parity;
+    // stage 1 also evaluates the external edge state of the next time level
+    // (used by stage 2 and by stage 1 of the next step); the interior
+    // blocks of the middle of the domain take it
+    if (STAGE == 1) {
+        const int b = blk + nblocks / 2 < nblocks ? blk + nblocks / 2 : blk + nblocks / 2 - nblocks;
+        edge_fill(a, k.par ^ 1, 1, b * (kWarps * 32) + threadIdx.x, nblocks * (kWarps * 32));
+    }
     k.out_lane = lane >= 2 && lane < 2 + kStrip && k.i < a.nx;
     k.dt = (float)a.ctl->dt;
     k.rho_ratio = (float)a.clk.rho_ratio;
@@ -439,7 +466,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         for (int r = j0 - 2; r <= j1 + 1; r++) {
             if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, nxt);
             Cell<float> c;
-            decode_cell<STAGE>(a, par, i, r, cur, c);
+            decode_cell<STAGE>(a, i, r, cur, c);
             // which parts this row runs (warp-uniform): see march_row
             march_row<STAGE>(a, k, r, c, w, KAHAN, r >= j0 && r < j1, r >= j0, r >= j0 + 1, r >= j0 + 2);
             cur = nxt;
@@ -551,6 +578,20 @@ int batch_grid_blocks() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<2>, kWarps * 32, 0);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
+}
+
+// The external edge state of the current time level (stage-1 brackets).
+__global__ void __launch_bounds__(256) edge_fill_kernel(const StageArgs<float> a) {
+    edge_fill(a, a.ctl->parity, 0, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+long long edge_floats(int nx, int ny) { return 2LL * 12 * ((long long)nx + ny); }
+
+cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st) {
+    if (!a.edge || a.bnd.n <= 0) return cudaSuccess;
+    const int total = 4 * (a.nx + a.ny);
+    edge_fill_kernel<<<(total + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st) {
