@@ -310,45 +310,82 @@ __device__ __forceinline__ void bracket(const double *times, int n, double t, in
     *s = (t - times[lo]) / (times[lo + 1] - times[lo]);
 }
 
-__device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
-                             const ForcingDev &wind, double speed, int mode) {
-    ctl->last_speed = speed;
-    if (mode == 1) { ctl->t += ctl->dt; ctl->step += 1; ctl->parity ^= 1; }
-    if (clk.dt_fixed > 0.0) {
-        ctl->dt = clk.dt_fixed;
-    } else if (mode == 0 || (mode == 1 && ctl->step % clk.dt_every == 0)) {
-        if (speed > 0.0 && isfinite(speed)) {
-            ctl->dt = clk.courant * 0.25 / speed;
-        } else if (ctl->err == ERR_NONE) {
-            ctl->err = ERR_NUMERIC;
-            ctl->err_step = ctl->step;
+// bracket(), trying the interval `hint` first: the forcing time only moves
+// forward, so the interval of the previous evaluation nearly always holds
+// (the frame times are strictly increasing, so the interval is unique and
+// both routes give the same k and s).
+__device__ __forceinline__ void bracket_hint(const double *times, int n, double t, int hint, int *k,
+                                             double *s) {
+    if (n > 1 && hint >= 0 && hint < n - 1) {
+        const double t0 = times[hint], t1 = times[hint + 1];
+        if (t0 <= t && t < t1) {
+            *k = hint;
+            *s = (t - t0) / (t1 - t0);
+            return;
         }
     }
-    // a forecast horizon: clip the last step to land on t_end, then stop
-    if (ctl->t_end > 0.0) {
-        if (ctl->t >= ctl->t_end * (1.0 - 1e-14)) ctl->done = 1;
-        else if (ctl->t + ctl->dt > ctl->t_end) ctl->dt = ctl->t_end - ctl->t;
+    bracket(times, n, t, k, s);
+}
+
+// Advance (mode 1) or set up (mode 0: dt from `speed`; mode 2: brackets
+// only) the clock. It runs on one thread at the end of every step, so the
+// state is read once into registers and written once at the end, and the
+// loads that do not depend on each other are issued together.
+__device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
+                             const ForcingDev &wind, double speed, int mode) {
+    double t = ctl->t, dt = ctl->dt;
+    long long step = ctl->step;
+    int parity = ctl->parity, done = ctl->done;
+    const int err0 = ctl->err;
+    const double t_end = ctl->t_end;
+    const int bhint = ctl->bk[1], whint = ctl->wk[1];
+    int err = err0;
+    if (mode == 1) { t += dt; step += 1; parity ^= 1; }
+    if (clk.dt_fixed > 0.0) {
+        dt = clk.dt_fixed;
+    } else if (mode == 0 || (mode == 1 && step % clk.dt_every == 0)) {
+        if (speed > 0.0 && isfinite(speed)) dt = clk.courant * 0.25 / speed;
+        else if (err == ERR_NONE) err = ERR_NUMERIC;
     }
-    for (int s = 0; s < 2; s++) {
-        double tt = ctl->t + (s ? ctl->dt : 0.0);
-        bracket(bnd.times, bnd.n, tt, &ctl->bk[s], &ctl->bs[s]);
-        bracket(wind.times, wind.n, tt, &ctl->wk[s], &ctl->ws[s]);
-        ctl->tau[s][0] = ctl->tau[s][1] = 0.0;
+    // a forecast horizon: clip the last step to land on t_end, then stop
+    if (t_end > 0.0) {
+        if (t >= t_end * (1.0 - 1e-14)) done = 1;
+        else if (t + dt > t_end) dt = t_end - t;
+    }
+    int bk[2], wk[2];
+    double bs[2], ws[2], tau[2][2];
+    for (int q = 0; q < 2; q++) {
+        const double tt = t + (q ? dt : 0.0);
+        bracket_hint(bnd.times, bnd.n, tt, bhint, &bk[q], &bs[q]);
+        bracket_hint(wind.times, wind.n, tt, whint, &wk[q], &ws[q]);
+        tau[q][0] = tau[q][1] = 0.0;
         if (wind.n > 0 && clk.wind_uniform) {
-            const float *A = wind.frames + 2LL * ctl->wk[s];
+            const float *A = wind.frames + 2LL * wk[q];
             const float *B = wind.n > 1 ? A + 2 : A;
-            double w = ctl->ws[s];
+            double w = ws[q];
             double wx = (1.0 - w) * A[0] + w * B[0];
             double wy = (1.0 - w) * A[1] + w * B[1];
             double sp = sqrt(wx * wx + wy * wy);
             double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
             double k = clk.rho_ratio * cdrag * sp;
-            ctl->tau[s][0] = k * wx;
-            ctl->tau[s][1] = k * wy;
+            tau[q][0] = k * wx;
+            tau[q][1] = k * wy;
         }
-        ctl->bs_f[s] = (float)ctl->bs[s];
-        ctl->tau_f[s][0] = (float)ctl->tau[s][0];
-        ctl->tau_f[s][1] = (float)ctl->tau[s][1];
+    }
+    ctl->last_speed = speed;
+    ctl->t = t;
+    ctl->dt = dt;
+    ctl->step = step;
+    ctl->parity = parity;
+    ctl->done = done;
+    if (err != err0) { ctl->err = err; ctl->err_step = step; }
+    for (int q = 0; q < 2; q++) {
+        ctl->bk[q] = bk[q]; ctl->bs[q] = bs[q];
+        ctl->wk[q] = wk[q]; ctl->ws[q] = ws[q];
+        ctl->tau[q][0] = tau[q][0]; ctl->tau[q][1] = tau[q][1];
+        ctl->bs_f[q] = (float)bs[q];
+        ctl->tau_f[q][0] = (float)tau[q][0];
+        ctl->tau_f[q][1] = (float)tau[q][1];
     }
 }
 
