@@ -120,6 +120,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float) -> float:
+    """The maximum of x over the ranks of the default process group (x
+    itself without one): the job time is that of the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world_size: int) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank advances its own replica of the workload)."""
+    return units_per_rank * world_size / max_over_ranks(seconds)
+
+
 def measured_hbm_peak():
     try:
         with open(PEAKS_FILE) as fh:
@@ -155,7 +174,7 @@ def committed_traffic(kernel: str):
 
 
 def algorithmic_bytes(wl, precision):
-    """Bytes each launch must move ('Roofline'): a water cell
+    """Algorithmic bytes each launch must move: a water cell
     reads its state, its bathymetry corner and the f / theta planes and
     writes its result; a land cell only needs its corner to know it is land.
     Halo re-reads and forcing frames are not counted."""
@@ -263,12 +282,8 @@ def run_ours(args):
     info = dom.info()
     launches = info.launches - launches0
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    device_s = float(step_ms.sum()) / 1e3
-    if ws > 1:
-        t = torch.tensor([device_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        device_s = float(t.item())
-    value = cells * args.steps * ws / device_s
+    device_s = max_over_ranks(float(step_ms.sum()) / 1e3)
+    value = whole_job_rate(cells * args.steps, device_s, ws)
 
     # back-to-back steps without flushing (how a forecast actually runs)
     torch.cuda.synchronize()
@@ -294,12 +309,8 @@ def run_ours(args):
     dom.step(args.steps)
     for f, hbuf in zip(fields, host_out):
         swe._check(dom._L.swe_read_state(dom.h, f, hbuf.data_ptr(), 0), "swe_read_state")
-    e2e_s = time.perf_counter() - e2e_t0
+    e2e_s = max_over_ranks(time.perf_counter() - e2e_t0)
     e2e_info = dom.info()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
     bytes_state = 3 * cells * 4
 
     # roofline of the dominant kernel
@@ -344,7 +355,7 @@ def run_ours(args):
             "back_to_back_ms_per_step": b2b_ms,
             "back_to_back_value": cells / (b2b_ms * 1e-3),
             "cpu_baseline": cpu,
-            "e2e": {"value": cells * args.steps * ws / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_rate(cells * args.steps, e2e_s, ws), "unit": UNIT,
                     "h2d_bytes_per_step": bytes_state / args.steps,
                     "d2h_bytes_per_step": bytes_state / args.steps,
                     "job": f"upload state from pinned host, {args.steps} steps, download state"},
