@@ -479,6 +479,100 @@ def run_serve(args):
     print(json.dumps(st), flush=True)
 
 
+def run_prep(args):
+    """Grid pre-processing kernels (Sections 3.8, 3.9), FP32, on inputs larger
+    than L2: corner bathymetry (4096^2 and 8192^2, 10 iterations), land
+    erosion (8192^2), refinement 8192^2 -> 16384^2 and coarsening back."""
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+    build.build()
+    swe.load()
+    st = torch.cuda.current_stream()
+    peak, peak_src = measured_hbm_peak()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    res = {}
+    rng = np.random.default_rng(1912_02457 + 8000)
+    # corner bathymetry: per iteration the residual (Hm, corners -> dH), the
+    # slopes (dH -> sx, sy), the corner estimate (dH, sx, sy, corners -> tmp)
+    # and the smoothing (tmp, corners -> corners): 14 floats = 56 B per cell
+    it = 10
+    for n in (4096, 8192):
+        z = synth.spectral_field(rng, n, n, max_fft=n + 1)
+        Hm = torch.from_numpy((5.0 + 2995.0 * ((z - z.min()) / (z.max() - z.min())) ** 2)
+                              .astype(np.float32)).cuda()
+        Hc = torch.empty((n + 1, n + 1), dtype=torch.float32, device="cuda")
+        work = torch.empty(swe.bathymetry_work_bytes(n, n), dtype=torch.uint8, device="cuda")
+        t0 = timed(lambda: swe.bathymetry_reconstruct(Hm.data_ptr(), n, n, n, Hc.data_ptr(), n + 1,
+                                                      work.data_ptr(), n_iter=0, stats=False,
+                                                      stream=st.cuda_stream), 5)
+        t10 = timed(lambda: swe.bathymetry_reconstruct(Hm.data_ptr(), n, n, n, Hc.data_ptr(), n + 1,
+                                                       work.data_ptr(), n_iter=it, stats=False,
+                                                       stream=st.cuda_stream), 5)
+        per_it = (t10 - t0) / it
+        gbs = 56.0 * n * n / per_it / 1e9
+        res[f"bathymetry_{n}"] = {"grid": f"{n}x{n}", "dtype": "f32", "iterations": it,
+                                  "ms_total": t10 * 1e3, "ms_per_iteration": per_it * 1e3,
+                                  "cell_iterations_per_s": n * n / per_it,
+                                  "achieved_gbs": gbs, "frac": gbs / peak, "bytes_per_cell_iteration": 56}
+        del Hm, Hc, work
+    # land erosion: 1 + 4 + 4 B in, 1 + 4 + 4 B out per cell
+    n = 8192
+    land = torch.from_numpy((rng.random((n, n)) < 0.3).astype(np.uint8)).cuda()
+    eta = torch.randn((n, n), dtype=torch.float32, device="cuda")
+    Hm = torch.rand((n, n), dtype=torch.float32, device="cuda")
+    lo, eo, ho = torch.empty_like(land), torch.empty_like(eta), torch.empty_like(Hm)
+    t = timed(lambda: swe.land_erode(land.data_ptr(), eta.data_ptr(), Hm.data_ptr(), n, n, n,
+                                     lo.data_ptr(), eo.data_ptr(), ho.data_ptr(), stream=st.cuda_stream), 10)
+    gbs = 18.0 * n * n / t / 1e9
+    res["land_erode"] = {"grid": f"{n}x{n}", "dtype": "f32", "ms": t * 1e3, "achieved_gbs": gbs,
+                         "frac": gbs / peak, "bytes_per_cell": 18}
+    del land, eta, Hm, lo, eo, ho
+    # refinement / coarsening: per coarse cell 3 x 4 B + a corner in, 3 x 16 B + 4 corners out
+    wl = synth.coastal(n, n, dtype=np.float32)
+    q = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (wl.eta, wl.hu, wl.hv)]
+    H = torch.from_numpy(np.ascontiguousarray(wl.H)).cuda()
+    qf = [torch.empty((2 * n, 2 * n), dtype=torch.float32, device="cuda") for _ in range(3)]
+    Hf = torch.empty((2 * n + 1, 2 * n + 1), dtype=torch.float32, device="cuda")
+    qp, qfp = [a.data_ptr() for a in q], [a.data_ptr() for a in qf]
+    t = timed(lambda: swe.refine2(qp, n, H.data_ptr(), n + 1, n, n, qfp, 2 * n, Hf.data_ptr(), 2 * n + 1,
+                                  stream=st.cuda_stream), 10)
+    gbs = 80.0 * n * n / t / 1e9
+    res["refine2"] = {"grid": f"{n}x{n} -> {2 * n}x{2 * n}", "dtype": "f32", "ms": t * 1e3,
+                      "achieved_gbs": gbs, "frac": gbs / peak, "bytes_per_coarse_cell": 80}
+    t = timed(lambda: swe.coarsen2(qfp, 2 * n, Hf.data_ptr(), 2 * n + 1, n, n, qp, n, H.data_ptr(), n + 1,
+                                   stream=st.cuda_stream), 10)
+    gbs = 80.0 * n * n / t / 1e9
+    res["coarsen2"] = {"grid": f"{2 * n}x{2 * n} -> {n}x{n}", "dtype": "f32", "ms": t * 1e3,
+                       "achieved_gbs": gbs, "frac": gbs / peak, "bytes_per_coarse_cell": 80}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import prep
+        m = 1024
+        zs = synth.spectral_field(np.random.default_rng(1912_02457 + 8001), m, m).astype(np.float64)
+        c0 = time.perf_counter()
+        prep.reconstruct_bathymetry(zs, n_iter=10)
+        cel = time.perf_counter() - c0
+        cpu = {"value": m * m * 10 / cel, "unit": "cell-iterations/s", "cores": 1, "kind": "oracle",
+               "sample": f"numpy oracle, corner bathymetry {m}x{m}, 10 iterations ({cel:.1f} s)"}
+    line = {"metric": METRIC, "workload": "grid pre-processing (Sections 3.8, 3.9)", "unit": "GB/s",
+            "peak_gbs": peak, "peak_source": peak_src, "results": res,
+            "cpu_baseline": cpu, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,7 +582,7 @@ def main():
     ap.add_argument("--precision", choices=("f32", "f32_kahan"), default="f32_kahan")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve"),
+    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep"),
                     default="coastal1024")
     ap.add_argument("--domains", type=int, default=64)
     ap.add_argument("--requests", type=int, default=48)
@@ -505,6 +599,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "prep":
+        return run_prep(args)
     return run_ours(args)
 
 

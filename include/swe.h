@@ -272,6 +272,71 @@ int swe_diagnostics_noalloc(const float *eta, const float *hu, const float *hv, 
                             int nx, int ny, long long pitch, long long cpitch, double dx,
                             double dy, double g, double kappa, double *out, void *stream);
 
+/* ---- grid pre-processing (Sections 3.8 and 3.9) -------------------------
+ * Run once before a simulation; all planes are device memory, row-major with
+ * the given row pitch in elements, and the work is stream-ordered on
+ * `stream`. Nothing is allocated. Corner planes carry SWE_LAND at land
+ * intersections where stated. Errors: SWE_ERR_INVALID_ARG for a NULL
+ * pointer, a size < 1, a pitch shorter than its row, or a parameter out of
+ * range; SWE_ERR_CUDA for a failed launch or copy. */
+
+/* Corner (bilinear) bathymetry from cell averages, Section 3.8 (FP32, the
+ * precision of the stage kernels that read the corners): the initial
+ * guess of eqn:recon_1 - eqn:recon_3 (limited cell slopes, each cell's plane
+ * at its corners, the mean of the estimates meeting at an intersection),
+ * then n_iter iterations of: dH = Hm - (mean of each cell's corners), add
+ * the eqn:recon_1 - eqn:recon_3 corner estimate of dH, smooth the corners.
+ *   Hm:    ny x nx cell averages (FP32), pitch >= nx;
+ *   Hc:    (ny+1) x (nx+1) corners (FP32 output), cpitch >= nx+1;
+ *   work:  swe_bathymetry_work_bytes(nx, ny) bytes of device scratch,
+ *          256-byte aligned;
+ *   theta: generalised-minmod parameter of the slopes, 1 <= theta <= 2;
+ *   smooth: weight w of the smoothing pass Hc := (1-w) Hc + w (mean of the
+ *          4 neighbour corners), 0 <= w <= 1; beyond an edge a cell or a
+ *          corner is linearly extrapolated, so a linear surface is exact;
+ *   stats: NULL, or a host array of 2 n_iter doubles that receives, per
+ *          iteration, max|Hm - cell mean of Hc| and max|corner change|
+ *          (the call then synchronises `stream`). */
+size_t swe_bathymetry_work_bytes(int nx, int ny);
+int swe_bathymetry_reconstruct(const float *Hm, long long pitch, int nx, int ny, float *Hc,
+                               long long cpitch, void *work, int n_iter, double theta,
+                               double smooth, double *stats, void *stream);
+
+/* One step of land erosion for narrow straits, Section 3.8: a land cell
+ * stays land only if its four neighbours are land (outside the domain
+ * counts as land); a cell it opens takes the largest eta of its water
+ * neighbours (gray dilation) and the depth land_depth (5 m in the paper).
+ *   land, land_out: ny x nx bytes (nonzero = land); eta, Hm in, eta_out,
+ *   Hm_out out (FP32); every plane has row pitch `pitch` elements; outputs
+ *   must not alias inputs. */
+int swe_land_erode(const unsigned char *land, const float *eta, const float *Hm,
+                   long long pitch, int nx, int ny, double land_depth,
+                   unsigned char *land_out, float *eta_out, float *Hm_out, void *stream);
+
+/* Refinement by two, Section 3.9 (FP32): every water cell's slope-limited
+ * reconstruction (generalised minmod with theta; a land or out-of-domain
+ * neighbour gives a zero difference) evaluated at its four children's
+ * centres; the corner surface evaluated at the fine intersections (coarse
+ * corner, mean of two, mean of four; SWE_LAND if any of them is). Children
+ * of land cells are land with zero state.
+ *   eta, hu, hv: ny x nx, pitch; H: (ny+1) x (nx+1) corners, cpitch;
+ *   eta_f, hu_f, hv_f: 2ny x 2nx, fpitch (even); H_f: (2ny+1) x (2nx+1),
+ *   fcpitch. Fine outputs start on 8-byte boundaries. */
+int swe_refine2(const float *eta, const float *hu, const float *hv, long long pitch,
+                const float *H, long long cpitch, int nx, int ny, double theta,
+                float *eta_f, float *hu_f, float *hv_f, long long fpitch, float *H_f,
+                long long fcpitch, void *stream);
+
+/* Coarsening by two, Section 3.9 (FP32): a coarse cell is the mean of its
+ * water children (zero if it is land, i.e. one of its sampled corners is
+ * SWE_LAND, or has none); the coarse corners are the even fine corners.
+ *   fine: 2ny x 2nx planes with fpitch (even), (2ny+1) x (2nx+1) corners with
+ *   fcpitch; coarse outputs ny x nx with pitch, (ny+1) x (nx+1) with cpitch.
+ *   Fine planes start on 8-byte boundaries. */
+int swe_coarsen2(const float *eta_f, const float *hu_f, const float *hv_f, long long fpitch,
+                 const float *H_f, long long fcpitch, int nx, int ny, float *eta, float *hu,
+                 float *hv, long long pitch, float *H, long long cpitch, void *stream);
+
 /* The last CUDA error string recorded by this thread, or "". */
 const char *swe_last_cuda_error(void);
 const char *swe_status_string(int status);

@@ -35,6 +35,8 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
+int swe::record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 struct swe_domain {
     int nx = 0, ny = 0, prec = 0;
     size_t esz = 4;

@@ -37,4 +37,7 @@ cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st);
 long long edge_floats(int nx, int ny);   // both time levels
 int diag_blocks(int nx, int ny);
 
+// Record e for swe_last_cuda_error and return SWE_ERR_CUDA (swe_capi.cu).
+int record_cuda_error(cudaError_t e);
+
 }  // namespace swe

@@ -100,9 +100,65 @@ SIGNATURES = {
                                           C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                                           C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.c_void_p, C.c_void_p]),
+    "swe_bathymetry_work_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "swe_bathymetry_reconstruct": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_void_p,
+                                             C.c_longlong, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                             C.c_void_p, C.c_void_p]),
+    "swe_land_erode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_int,
+                                 C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "swe_refine2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
+                              C.c_longlong, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_longlong, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "swe_coarsen2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
+                               C.c_longlong, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_longlong, C.c_void_p, C.c_longlong, C.c_void_p]),
 }
 
 NOALLOC_MAX_ROWS = 16384
+
+
+# ---- grid pre-processing: device pointers and pitches in elements (swe.h)
+
+def bathymetry_work_bytes(nx, ny):
+    return int(load().swe_bathymetry_work_bytes(int(nx), int(ny)))
+
+
+def bathymetry_reconstruct(Hm_ptr, pitch, nx, ny, Hc_ptr, cpitch, work_ptr, n_iter=10,
+                           theta=1.3, smooth=0.125, stats=True, stream=0):
+    """Corner bathymetry from FP64 cell averages; returns, when `stats`, an
+    (n_iter, 2) array of the per-iteration midpoint misfit and corner change."""
+    out = np.zeros(2 * max(int(n_iter), 1), dtype=np.float64) if stats else None
+    _check(load().swe_bathymetry_reconstruct(
+        C.c_void_p(Hm_ptr), int(pitch), int(nx), int(ny), C.c_void_p(Hc_ptr), int(cpitch),
+        C.c_void_p(work_ptr), int(n_iter), float(theta), float(smooth),
+        out.ctypes.data_as(C.c_void_p) if stats else None, C.c_void_p(stream)),
+        "swe_bathymetry_reconstruct")
+    return out[:2 * int(n_iter)].reshape(-1, 2) if stats else None
+
+
+def land_erode(land_ptr, eta_ptr, Hm_ptr, pitch, nx, ny, land_out_ptr, eta_out_ptr, Hm_out_ptr,
+               land_depth=5.0, stream=0):
+    _check(load().swe_land_erode(C.c_void_p(land_ptr), C.c_void_p(eta_ptr), C.c_void_p(Hm_ptr),
+                                 int(pitch), int(nx), int(ny), float(land_depth),
+                                 C.c_void_p(land_out_ptr), C.c_void_p(eta_out_ptr),
+                                 C.c_void_p(Hm_out_ptr), C.c_void_p(stream)), "swe_land_erode")
+
+
+def refine2(q_ptrs, pitch, H_ptr, cpitch, nx, ny, qf_ptrs, fpitch, Hf_ptr, fcpitch, theta=1.3,
+            stream=0):
+    """q_ptrs / qf_ptrs: device pointers of (eta, hu, hv), coarse / fine."""
+    _check(load().swe_refine2(*(C.c_void_p(p) for p in q_ptrs), int(pitch), C.c_void_p(H_ptr),
+                              int(cpitch), int(nx), int(ny), float(theta),
+                              *(C.c_void_p(p) for p in qf_ptrs), int(fpitch), C.c_void_p(Hf_ptr),
+                              int(fcpitch), C.c_void_p(stream)), "swe_refine2")
+
+
+def coarsen2(qf_ptrs, fpitch, Hf_ptr, fcpitch, nx, ny, q_ptrs, pitch, H_ptr, cpitch, stream=0):
+    """nx, ny: the coarse size; the fine planes are 2ny x 2nx."""
+    _check(load().swe_coarsen2(*(C.c_void_p(p) for p in qf_ptrs), int(fpitch), C.c_void_p(Hf_ptr),
+                               int(fcpitch), int(nx), int(ny), *(C.c_void_p(p) for p in q_ptrs),
+                               int(pitch), C.c_void_p(H_ptr), int(cpitch), C.c_void_p(stream)),
+           "swe_coarsen2")
 
 
 def diagnostics_noalloc(eta_ptr, hu_ptr, hv_ptr, H_ptr, nx, ny, pitch, cpitch, dx, dy,
