@@ -175,7 +175,7 @@ class Oracle:
         p = wl.params
         if state is None:
             state = (wl.eta, wl.hu, wl.hv)
-        e, u, v = (np.array(a, dtype=np.float64, copy=True) for a in state)
+        e, u, v = (np.array(a, dtype=np.float64, order="C", copy=True) for a in state)
         tt = C.c_double(wl.t0 if t is None else t)
         dd = C.c_double(dt)
         dts = np.zeros(max(n_steps, 1))

@@ -39,7 +39,7 @@
 #define ORC_LAND ((double)FLT_MAX)
 
 enum { ORC_S = 0, ORC_N = 1, ORC_W = 2, ORC_E = 3 };
-enum { ORC_WALL = 0, ORC_NESTED = 1 };
+enum { ORC_WALL = 0, ORC_NESTED = 1, ORC_PERIODIC = 2 };
 
 typedef struct {
     int nx, ny;
@@ -51,7 +51,8 @@ typedef struct {
     double rho_air, rho_water;
     double frs_d0;      /* flow-relaxation fall-off d0, eq:frs */
     int frs_width;      /* cells of the relaxation zone */
-    int bc[4];          /* S, N, W, E: ORC_WALL or ORC_NESTED */
+    int bc[4];          /* S, N, W, E: ORC_WALL, ORC_NESTED or ORC_PERIODIC
+                           (periodic edges come in opposite pairs) */
     const double *H;    /* (ny+1)*(nx+1) corner depths */
     const double *f;    /* ny*nx Coriolis parameter */
     const double *theta;/* ny*nx north angle */
@@ -216,6 +217,25 @@ static int refl(int i, int n)
     return i;
 }
 
+/* Periodic boundaries (Section 3.3 names them beside walls): the padded
+ * corner i is the periodic image i mod n of the input corner line (the input's
+ * last corner line repeats its first), and a ghost cell is the periodic image
+ * of an interior cell with all its statics and state. */
+static int corner_src(int i, int n, int periodic)
+{
+    if (!periodic) return refl(i, n);
+    while (i < 0) i += n;
+    while (i > n) i -= n;
+    return i;
+}
+
+static int wrap(int i, int n)
+{
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
+}
+
 static void statics_free(statics *S)
 {
     free(S->Hc); free(S->f); free(S->ct); free(S->st); free(S->land);
@@ -255,9 +275,14 @@ static int statics_build(const orc_domain *d, statics *S)
     if (!S->Hc || !S->f || !S->ct || !S->st || !S->land || !S->HE || !S->HW ||
         !S->HN || !S->HS || !S->Hbar) { statics_free(S); return -1; }
 
+    const int px = d->bc[ORC_W] == ORC_PERIODIC, py = d->bc[ORC_S] == ORC_PERIODIC;
+    if (px != (d->bc[ORC_E] == ORC_PERIODIC) || py != (d->bc[ORC_N] == ORC_PERIODIC)) {
+        statics_free(S);
+        return -1;                              /* a periodic edge needs its opposite */
+    }
     for (int j = -2; j <= ny + 2; j++)
         for (int i = -2; i <= nx + 2; i++)
-            S->Hc[KI(S, i, j)] = d->H[(size_t)refl(j, ny) * (nx + 1) + refl(i, nx)];
+            S->Hc[KI(S, i, j)] = d->H[(size_t)corner_src(j, ny, py) * (nx + 1) + corner_src(i, nx, px)];
 
     for (int j = -2; j <= ny + 1; j++)
         for (int i = -2; i <= nx + 1; i++) {
@@ -296,9 +321,11 @@ static int statics_build(const orc_domain *d, statics *S)
                 int e = ghost_source(nx, ny, i, j, &si, &sj, &row);
                 if (e < 0 || row != ring) continue;
                 size_t c = CI(S, i, j), s = CI(S, si, sj);
+                if (d->bc[e] == ORC_PERIODIC) s = CI(S, wrap(i, nx), wrap(j, ny));
                 /* Section 3.3: at a wall the Coriolis parameter is odd,
                  * f(-x) = -f(x), so that K_x = 0 across the wall. Nested
-                 * edges continue f evenly (reading). */
+                 * edges continue f evenly (reading); a periodic ghost is its
+                 * periodic image. */
                 S->f[c] = d->bc[e] == ORC_WALL ? -S->f[s] : S->f[s];
                 S->ct[c] = S->ct[s];
             }
@@ -313,7 +340,8 @@ static int statics_build(const orc_domain *d, statics *S)
 /* Ghost cells of the state at time t (Sections 3.3 and 3.6): walls mirror
  * the first two interior cells (eta even, normal momentum odd, tangential
  * momentum even, eq:tradWallBCx); nested edges take the external solution
- * interpolated in time and along the edge. */
+ * interpolated in time and along the edge; periodic edges take the periodic
+ * image. */
 static void fill_ghosts(const orc_domain *d, const statics *S,
                         double *eta, double *hu, double *hv, double t)
 {
@@ -328,7 +356,10 @@ static void fill_ghosts(const orc_domain *d, const statics *S,
             if (e == -2) { eta[c] = hu[c] = hv[c] = NAN; continue; }
             if (row != ring) continue;
             size_t s = CI(S, si, sj);
-            if (d->bc[e] == ORC_WALL) {
+            if (d->bc[e] == ORC_PERIODIC) {
+                s = CI(S, wrap(i, nx), wrap(j, ny));
+                eta[c] = eta[s]; hu[c] = hu[s]; hv[c] = hv[s];
+            } else if (d->bc[e] == ORC_WALL) {
                 eta[c] = eta[s];
                 if (e == ORC_W || e == ORC_E) { hu[c] = -hu[s]; hv[c] = hv[s]; }
                 else                          { hu[c] = hu[s];  hv[c] = -hv[s]; }

@@ -36,6 +36,7 @@ LAND = float(np.finfo(np.float32).max)
 
 BC_WALL = 0
 BC_NESTED = 1
+BC_PERIODIC = 2      # opposite edges pair up; the corner plane's last line repeats its first
 EDGES = ("S", "N", "W", "E")
 
 OMEGA = 7.2921e-5   # Earth's rotation rate (Section 3.7)
@@ -363,6 +364,51 @@ def peaks_convergence(n: int, dtype=np.float64, bump_radius_km: float = 300.0
 
 
 SWEEP_SIZES = ((512, 512), (2048, 2048), (2600, 900), (4096, 4096), (8192, 8192))
+
+
+def beta_plane_f(nx: int, ny: int, dx: float, dy: float, f_ref: float, beta: float,
+                 theta: float, x_ref: float = None, y_ref: float = None) -> np.ndarray:
+    """Coriolis parameter of a beta plane (eq:betaplane): f_ref plus beta
+    times the distance from (x_ref, y_ref) (default: the domain centre) along
+    the north vector n = [sin theta, cos theta]; cell centres at ((i+1/2) dx,
+    (j+1/2) dy). An input plane of the workload."""
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    x_ref = nx * dx / 2.0 if x_ref is None else x_ref
+    y_ref = ny * dy / 2.0 if y_ref is None else y_ref
+    return f_ref + beta * (np.sin(theta) * (x[None, :] - x_ref) + np.cos(theta) * (y[:, None] - y_ref))
+
+
+def rossby(n: int = 350, dx: float = 20e3, depth: float = 50.0, f_ref: float = 8e-5,
+           beta: float = 2e-11, theta: float = 0.0, amp: float = 0.1, radius_cells: float = 10.0,
+           dtype=np.float64, days: float = 35.0) -> Workload:
+    """Planetary Rossby waves (Section 3.7, the beta-plane experiment): n x n
+    cells of dx = 20 km, flat depth 50 m, periodic on every edge, a beta
+    plane around the domain centre (f_ref = 8e-5 1/s, the value of ~33 N;
+    beta = 2e-11 1/(m s)) along the north angle theta, and a Gaussian bump of
+    eta (amplitude `amp`, sigma `radius_cells`) at the centre in geostrophic
+    balance with f_ref: hu = -(g h / f) d(eta)/dy, hv = (g h / f) d(eta)/dx."""
+    g = 9.81
+    c = n / 2.0
+    j, i = np.mgrid[0:n, 0:n]
+    X = (i + 0.5 - c) * dx
+    Y = (j + 0.5 - c) * dx
+    R = radius_cells * dx
+    eta = amp * np.exp(-(X * X + Y * Y) / (2.0 * R * R))
+    detadx = -X / (R * R) * eta
+    detady = -Y / (R * R) * eta
+    h = depth + eta
+    hu = -(g * h / f_ref) * detady
+    hv = (g * h / f_ref) * detadx
+    H = np.full((n + 1, n + 1), depth)
+    f = beta_plane_f(n, n, dx, dx, f_ref, beta, theta)
+    wl = Workload(name=f"rossby{n}", nx=n, ny=n, dx=dx, dy=dx,
+                  eta=eta.astype(dtype), hu=hu.astype(dtype), hv=hv.astype(dtype),
+                  H=H.astype(dtype), f=f.astype(dtype),
+                  theta=np.full((n, n), theta).astype(dtype),
+                  bc=(BC_PERIODIC,) * 4, params=Params(courant=0.8),
+                  horizon=days * 86400.0)
+    return wl
 
 
 def ensemble(n_domains: int = 64, seed_config: int = 4, hours: int = 24):

@@ -153,3 +153,39 @@ def front_set(wl, eta_end, depth=0.01, radius=3):
     land = wl.land_cells()
     dry = (((wl.eta.astype(np.float64) + Hbar) <= depth) | ((eta_end + Hbar) <= depth)) & ~land
     return max_filter(dry.astype(np.int8), radius).astype(bool) & ~land
+
+
+def periodic_rough(nx, ny, seed=0, land=False, periodic=(True, True), dtype=np.float64):
+    """Rough domain for periodic boundaries: a periodic random bathymetry
+    (its last corner row / column repeats the first along each periodic
+    axis), optional land blobs, varying f and north angle; walls on the
+    non-periodic axes. No forcing."""
+    from paper_1912_02457_gb300 import synth
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(ny)[:, None] ** 2 + np.fft.fftfreq(nx)[None, :] ** 2
+    spec = (rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))) / np.maximum(k, 2e-3) ** 1.0
+    z = np.real(np.fft.ifft2(spec))
+    z = (z - z.min()) / (z.max() - z.min())
+    Hc = np.empty((ny + 1, nx + 1))
+    Hc[:ny, :nx] = 20.0 + 200.0 * z
+    Hc[ny, :nx] = Hc[0, :nx] if periodic[1] else Hc[ny - 1, :nx]
+    Hc[:, nx] = Hc[:, 0] if periodic[0] else Hc[:, nx - 1]
+    if land:
+        lm = np.zeros((ny, nx), dtype=bool)
+        lm[ny // 3: ny // 3 + 4, nx // 4: nx // 4 + 5] = True
+        lm[-3:, -4:] = True                      # touches the seams
+        lm = synth.open_mask_2x2(lm)
+        Hc = synth.encode_land(Hc, lm)
+        if periodic[0]:
+            Hc[:, nx] = Hc[:, 0]
+        if periodic[1]:
+            Hc[ny, :] = Hc[0, :]
+    f = 1.0e-4 + 2e-5 * rng.standard_normal((ny, nx))
+    th = rng.uniform(-0.5, 0.5, (ny, nx))
+    bc = (synth.BC_PERIODIC if periodic[1] else synth.BC_WALL,) * 2 + \
+         (synth.BC_PERIODIC if periodic[0] else synth.BC_WALL,) * 2
+    z0 = np.zeros((ny, nx))
+    wl = synth.Workload(name=f"periodic{nx}x{ny}", nx=nx, ny=ny, dx=1000.0, dy=1000.0,
+                        eta=z0.copy(), hu=z0.copy(), hv=z0.copy(), H=Hc, f=f, theta=th,
+                        bc=bc, params=synth.Params())
+    return wl.astype(dtype)
