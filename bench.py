@@ -414,6 +414,32 @@ def run_sweep(args):
                       "unit": UNIT, "precision": args.precision, "results": out}), flush=True)
 
 
+def run_rossby(args):
+    """The beta-plane Rossby workload (350^2 cells of 20 km, periodic on every
+    edge, FP32 + Kahan) for two orientations of north: cell-updates/s of
+    back-to-back graph steps, stage times, and the simulated days per second."""
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+    build.build()
+    swe.load()
+    stream = torch.cuda.Stream()
+    out = []
+    for theta in (0.0, np.pi / 4):
+        wl = synth.rossby(n=350, theta=theta, dtype=np.float32)
+        with swe.Domain(wl, args.precision, stream=stream.cuda_stream) as d:
+            d.step(args.warmup)
+            el = _timed_steps(torch, d, args.steps, stream)
+            info = d.info()
+            ms = d.step_profiled(8).mean(axis=0)
+            out.append({"theta": theta, "steps": args.steps,
+                        "cell_updates_per_s": float(wl.nx * wl.ny * args.steps / el),
+                        "ms_per_step": el * 1e3 / args.steps, "dt_s": info.dt,
+                        "simulated_days_per_s": info.dt * args.steps / el / 86400.0,
+                        "stage_ms": {"stage1": float(ms[0]), "stage2": float(ms[1])}})
+    print(json.dumps({"metric": METRIC, "workload": "beta-plane Rossby waves, 350x350 periodic",
+                      "unit": UNIT, "precision": args.precision, "results": out}), flush=True)
+
+
 def run_ensemble(args):
     """64 domains of uneven sizes in one batch: one persistent launch per
     stage (graph-captured, autotuned tiles) against launching the same
@@ -582,7 +608,7 @@ def main():
     ap.add_argument("--precision", choices=("f32", "f32_kahan"), default="f32_kahan")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep"),
+    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep", "rossby"),
                     default="coastal1024")
     ap.add_argument("--domains", type=int, default=64)
     ap.add_argument("--requests", type=int, default=48)
@@ -601,6 +627,8 @@ def main():
         return run_serve(args)
     if args.workload == "prep":
         return run_prep(args)
+    if args.workload == "rossby":
+        return run_rossby(args)
     return run_ours(args)
 
 

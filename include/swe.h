@@ -47,7 +47,11 @@ typedef enum {
     SWE_F64 = 2         /* FP64 everywhere (parity build, not a fast path) */
 } swe_precision;
 
-typedef enum { SWE_BC_WALL = 0, SWE_BC_NESTED = 1 } swe_bc;
+/* Boundary of one edge. WALL: reflective (Section 3.3). NESTED: ghosts from
+ * the boundary frames with flow relaxation (Section 3.6). PERIODIC (Section
+ * 3.3): the opposite edge must be PERIODIC too, and the corner plane's last
+ * row (for S/N) or column (for W/E) must repeat its first. */
+typedef enum { SWE_BC_WALL = 0, SWE_BC_NESTED = 1, SWE_BC_PERIODIC = 2 } swe_bc;
 typedef enum { SWE_FORCING_WIND = 0, SWE_FORCING_BOUNDARY = 1 } swe_forcing_kind;
 
 typedef enum {

@@ -296,12 +296,39 @@ int validate(const swe_domain_desc *d, const swe_params *p) {
     if (!(d->dx > 0) || !(d->dy > 0)) return SWE_ERR_INVALID_ARG;
     if (d->precision < SWE_F32 || d->precision > SWE_F64) return SWE_ERR_INVALID_ARG;
     for (int e = 0; e < 4; e++)
-        if (d->bc[e] != SWE_BC_WALL && d->bc[e] != SWE_BC_NESTED) return SWE_ERR_INVALID_ARG;
+        if (d->bc[e] != SWE_BC_WALL && d->bc[e] != SWE_BC_NESTED && d->bc[e] != SWE_BC_PERIODIC)
+            return SWE_ERR_INVALID_ARG;
+    // periodic edges pair up (S with N, W with E)
+    if ((d->bc[0] == SWE_BC_PERIODIC) != (d->bc[1] == SWE_BC_PERIODIC) ||
+        (d->bc[2] == SWE_BC_PERIODIC) != (d->bc[3] == SWE_BC_PERIODIC))
+        return SWE_ERR_INVALID_ARG;
     if ((long long)d->nx * d->ny >= (1LL << 31)) return SWE_ERR_INVALID_ARG;
     // a nested edge mirrors the two cells next to it for the ghost statics
     if ((d->bc[2] == SWE_BC_NESTED || d->bc[3] == SWE_BC_NESTED) && d->nx < 2) return SWE_ERR_INVALID_ARG;
     if ((d->bc[0] == SWE_BC_NESTED || d->bc[1] == SWE_BC_NESTED) && d->ny < 2) return SWE_ERR_INVALID_ARG;
     if (!d->eta || !d->hu || !d->hv || !d->H) return SWE_ERR_INVALID_ARG;
+    // a periodic axis needs a corner plane whose last line repeats its first
+    // (checked where the plane is host memory)
+    if (!d->src_is_device) {
+        const size_t w = (size_t)d->nx + 1;
+        if (d->precision == SWE_F64) {
+            const double *H = static_cast<const double *>(d->H);
+            if (d->bc[2] == SWE_BC_PERIODIC)
+                for (int j = 0; j <= d->ny; j++)
+                    if (H[j * w] != H[j * w + d->nx]) return SWE_ERR_INVALID_ARG;
+            if (d->bc[0] == SWE_BC_PERIODIC)
+                for (int i = 0; i <= d->nx; i++)
+                    if (H[i] != H[(size_t)d->ny * w + i]) return SWE_ERR_INVALID_ARG;
+        } else {
+            const float *H = static_cast<const float *>(d->H);
+            if (d->bc[2] == SWE_BC_PERIODIC)
+                for (int j = 0; j <= d->ny; j++)
+                    if (H[j * w] != H[j * w + d->nx]) return SWE_ERR_INVALID_ARG;
+            if (d->bc[0] == SWE_BC_PERIODIC)
+                for (int i = 0; i <= d->nx; i++)
+                    if (H[i] != H[(size_t)d->ny * w + i]) return SWE_ERR_INVALID_ARG;
+        }
+    }
     if (p->frs_width < 0 || p->frs_width > swe::kMaxFrs) return SWE_ERR_INVALID_ARG;
     if (!(p->g > 0) || !(p->kappa > 0) || !(p->courant > 0) || !(p->frs_d0 > 0)) return SWE_ERR_INVALID_ARG;
     if (p->cd < 0 || p->theta_mm < 1.0 || p->theta_mm > 2.0) return SWE_ERR_INVALID_ARG;

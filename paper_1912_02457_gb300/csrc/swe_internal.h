@@ -10,7 +10,7 @@ namespace swe {
 constexpr int kMaxFrs = 32;          // deepest flow-relaxation zone supported
 constexpr float kLand = 3.40282346638528859812e+38f;  // FLT_MAX corner marker
 enum { EDGE_S = 0, EDGE_N = 1, EDGE_W = 2, EDGE_E = 3 };
-enum { BC_WALL = 0, BC_NESTED = 1 };
+enum { BC_WALL = 0, BC_NESTED = 1, BC_PERIODIC = 2 };
 enum { ERR_NONE = 0, ERR_NUMERIC = -4 };
 
 // Device-resident clock of one domain. The stage kernels read dt and the

@@ -28,7 +28,8 @@ __device__ __forceinline__ void sincos_t<double>(double x, double *s, double *c)
 // wall of Section 3.4, which equals the ghost mirror of Section 3.3).
 // Outside a nested edge it is a ghost cell: bathymetry, f and theta of the
 // mirrored interior cell (faces swapped), state from the external frames
-// at the stage time (Section 3.6).
+// at the stage time (Section 3.6). Outside a periodic edge it is the
+// periodic image of an interior cell (Section 3.3).
 template <typename T, int STAGE>
 __device__ __forceinline__ void load_cell(const StageArgs<T> &a, int par, int i, int j, Cell<T> &c) {
     const int nx = a.nx, ny = a.ny;
@@ -38,6 +39,14 @@ __device__ __forceinline__ void load_cell(const StageArgs<T> &a, int par, int i,
     else if (j < 0)   { e = EDGE_S; sj = -j - 1;         row = -j - 1; }
     else if (j >= ny) { e = EDGE_N; sj = 2 * ny - 1 - j; row = j - ny; }
     if (e >= 0 && a.bc[e] == BC_WALL) { c.land = true; return; }
+    if (e >= 0 && a.bc[e] == BC_PERIODIC) {
+        // the periodic image of an interior cell, statics and state alike
+        // (the stencil reaches at most two cells past an edge)
+        si = i; sj = j;
+        if (e >= EDGE_W) { si += si < 0 ? nx : -nx; si += si < 0 ? nx : (si >= nx ? -nx : 0); }
+        else             { sj += sj < 0 ? ny : -ny; sj += sj < 0 ? ny : (sj >= ny ? -ny : 0); }
+        e = -1;
+    }
     const long long cp = a.cpitch;
     const T *H = a.H + (long long)sj * cp + si;
     T c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];

@@ -102,7 +102,8 @@ __device__ void edge_fill(const StageArgs<float> &a, int slot, int stage, int id
 // of nested edges (Section 3.6: statics mirrored from the cells inside the
 // edge, external state from the edge-state buffer) take the same loads;
 // cells outside a wall, the ghost-ghost corners and lanes beyond the halo
-// of the last strip are land (all four corners LAND). Stage 2 adds the increment
+// of the last strip are land (all four corners LAND); a ghost of a periodic
+// edge is the periodic image of an interior cell. Stage 2 adds the increment
 // D1 to interior cells; a ghost adds -0.0f, which leaves every value as it
 // is.
 template <int STAGE>
@@ -120,6 +121,13 @@ __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, i
     else if (i >= nx) { e = EDGE_E; si = 2 * nx - 1 - i; ring = i - nx; }
     else if (r < 0)   { e = EDGE_S; sj = -r - 1;         ring = sj; }
     else if (r >= ny) { e = EDGE_N; sj = 2 * ny - 1 - r; ring = r - ny; }
+    if (e >= 0 && a.bc[e] == BC_PERIODIC) {
+        // the periodic image of an interior cell (at most two cells past the edge)
+        si = i; sj = r;
+        if (e >= EDGE_W) { si += si < 0 ? nx : -nx; si += si < 0 ? nx : (si >= nx ? -nx : 0); }
+        else             { sj += sj < 0 ? ny : -ny; sj += sj < 0 ? ny : (sj >= ny ? -ny : 0); }
+        e = -1;
+    }
     if ((ox && oy) || i < -2 || i > nx + 1 || (e >= 0 && a.bc[e] != BC_NESTED)) {
         w.c00 = w.c10 = w.c01 = w.c11 = kLand;
         return;
@@ -160,8 +168,10 @@ __device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int i, in
     c.Hbar = 0.25f * (w.c00 + w.c10 + w.c01 + w.c11);
     float HE = 0.5f * (w.c10 + w.c11), HW = 0.5f * (w.c00 + w.c01);
     float HN = 0.5f * (w.c01 + w.c11), HS = 0.5f * (w.c00 + w.c10);
-    // a ghost's statics are mirrored across its edge
-    const bool swap_x = (unsigned)i >= (unsigned)a.nx, swap_y = (unsigned)r >= (unsigned)a.ny;
+    // a nested ghost's statics are mirrored across its edge (a periodic
+    // ghost is its periodic image, unmirrored)
+    const bool swap_x = (unsigned)i >= (unsigned)a.nx && a.bc[EDGE_W] != BC_PERIODIC;
+    const bool swap_y = (unsigned)r >= (unsigned)a.ny && a.bc[EDGE_S] != BC_PERIODIC;
     c.HE = swap_x ? HW : HE; c.HW = swap_x ? HE : HW;
     c.HN = swap_y ? HS : HN; c.HS = swap_y ? HN : HS;
     c.f = w.f;
