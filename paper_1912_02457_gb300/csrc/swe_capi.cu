@@ -80,10 +80,9 @@ struct swe_domain {
         graph = nullptr;
     }
 
-    // one-entry tile table of the FP32 fast path (same kernel as batches)
-    swe::StageArgs<float> *t_args = nullptr;
-    int *t_start = nullptr, *t_gx = nullptr, *t_rows = nullptr, *t_n = nullptr;
-    int t_tiles = 0;
+    // the FP32 fast path: the domain's tiling and arguments, handed to the
+    // persistent stage kernel (the one batches use) with every launch
+    swe::OneDomain one{};
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
     int parts() const { return fast() ? swe::fast_step_parts() : swe::ref_step_parts(); }
@@ -170,30 +169,14 @@ StageArgs<T> make_args(const swe_domain *d) {
     return a;
 }
 
-// (Re)write the domain's own one-entry tile table (fast FP32 path).
+// (Re)compute the fast path's tiling and launch arguments (after creation
+// and whenever the forcing buffers change).
 int upload_table(swe_domain *d) {
     if (!d->fast()) return SWE_OK;
-    swe::StageArgs<float> a = make_args<float>(d);
-    int rows = swe::fast_rows(d->nx, d->ny), gx = 0;
-    d->t_tiles = swe::fast_tiles(d->nx, d->ny, rows, &gx);
-    int start[2] = {0, d->t_tiles}, one = 1;
-    CK(cudaStreamSynchronize(d->stream));
-    CK(cudaMemcpy(d->t_args, &a, sizeof a, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d->t_start, start, sizeof start, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d->t_gx, &gx, sizeof gx, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d->t_rows, &rows, sizeof rows, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d->t_n, &one, sizeof one, cudaMemcpyHostToDevice));
+    d->one.args = make_args<float>(d);
+    d->one.rows = swe::fast_rows(d->nx, d->ny);
+    d->one.tiles = swe::fast_tiles(d->nx, d->ny, d->one.rows, &d->one.strips);
     return SWE_OK;
-}
-
-swe::BatchTable own_table(const swe_domain *d) {
-    swe::BatchTable t;
-    t.args = d->t_args;
-    t.tile_start = d->t_start;
-    t.grid_x = d->t_gx;
-    t.rows = d->t_rows;
-    t.n_domains = d->t_n;
-    return t;
 }
 
 int upload_plane(swe_domain *d, void *dst, const void *src, int rows, int cols,
@@ -261,10 +244,6 @@ int create_impl(const swe_domain_desc *dd, const swe_params *p, void *stream, sw
         const size_t eb = (size_t)swe::edge_floats(d->nx, d->ny) * sizeof(float);
         if (!(d->edge = (float *)d->dalloc(eb))) return SWE_ERR_OOM;
         CK(cudaMemsetAsync(d->edge, 0, eb, d->stream));
-        if (!(d->t_args = (swe::StageArgs<float> *)d->dalloc(sizeof(swe::StageArgs<float>))) ||
-            !(d->t_start = (int *)d->dalloc(2 * sizeof(int))) || !(d->t_gx = (int *)d->dalloc(sizeof(int))) ||
-            !(d->t_rows = (int *)d->dalloc(sizeof(int))) || !(d->t_n = (int *)d->dalloc(sizeof(int))))
-            return SWE_ERR_OOM;
     }
     int nb = swe::diag_blocks(d->nx, d->ny);
     if (!(d->diag_partials = (double *)d->dalloc((size_t)nb * 2 * sizeof(double)))) return SWE_ERR_OOM;
@@ -450,7 +429,7 @@ int step_check(swe_handle h, int n_steps) {
 int launch_part_on(swe_handle h, int part, cudaStream_t st) {
     cudaError_t e;
     if (h->prec == SWE_F64) e = swe::launch_step_ref_part(make_args<double>(h), st, part, false);
-    else if (h->fast()) e = swe::launch_batch_stage(own_table(h), h->t_tiles, part + 1, st);
+    else if (h->fast()) e = swe::launch_domain_stage(h->one, part + 1, st);
     else e = swe::launch_step_ref_part(make_args<float>(h), st, part, h->prec == SWE_F32_KAHAN);
     if (e != cudaSuccess) return cuda_fail(e);
     return SWE_OK;

@@ -83,6 +83,13 @@ struct StageArgs {
     float *edge;
 };
 
+// A single FP32 domain handed to the persistent stage kernel with the launch
+// (kernel parameter space): tiles > 0 selects it over the batch table.
+struct OneDomain {
+    StageArgs<float> args;
+    int tiles, rows, strips;
+};
+
 // Device-resident tile table of a batch of FP32 domains (persistent kernel).
 struct BatchTable {
     const StageArgs<float> *args;   // per domain

@@ -31,6 +31,8 @@ int fast_rows(int nx, int ny);
 int fast_tiles(int nx, int ny, int rows, int *grid_x);
 int batch_grid_blocks();
 cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st);
+// The same kernel for one domain whose arguments travel with the launch.
+cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st);
 // Fill the external edge state of the current time level (after the clock
 // or the forcing was set); stage 1 of every step fills the next level.
 cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st);

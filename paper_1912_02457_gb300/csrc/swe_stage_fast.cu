@@ -15,6 +15,8 @@
 //    square root (-prec-div=false -prec-sqrt=false): ~1 ulp, far inside the
 //    parity tolerance, and exact zeros stay exact (lake at rest is still
 //    bit-exact).
+#include <cstring>
+
 #include "swe_device.cuh"
 #include "swe_kernels.h"
 
@@ -30,6 +32,11 @@ constexpr int kWarps = 4;            // warps per block
 #ifndef SWE_FORCE_ROWS
 #define SWE_FORCE_ROWS 0             // > 0: fixed tile height (tuning builds)
 #endif
+#ifndef SWE_UNROLL
+#define SWE_UNROLL 1                 // row iterations unrolled in the march
+#endif
+#define SWE_STR(x) #x
+#define SWE_UNROLL_PRAGMA(n) _Pragma(SWE_STR(unroll n))
 
 __device__ __forceinline__ void bnd_pos_f(int k, int n, int nb, int &k0, int &k1, float &w) {
     float p = (k + 0.5f) * (float)nb / (float)n - 0.5f;
@@ -473,6 +480,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         const int i = k.i, j0 = k.j0, j1 = k.j1, par = k.par;
         RawCell<STAGE> cur, nxt;
         fetch_cell<STAGE>(a, par, i, j0 - 2, cur);
+        SWE_UNROLL_PRAGMA(SWE_UNROLL)
         for (int r = j0 - 2; r <= j1 + 1; r++) {
             if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, nxt);
             Cell<float> c;
@@ -499,33 +507,46 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
 // Persistent batch kernel: each block walks the tile table of all domains
 // (tile t belongs to the domain d with tile_start[d] <= t < tile_start[d+1]).
 // The table lives in device memory, so a captured graph of this kernel stays
-// valid when domains are added, removed or retiled.
+// valid when domains are added, removed or retiled. A single domain comes
+// with the launch instead (`one`, tiles > 0): its arguments sit in the
+// kernel's parameter space, so a launch does not start with a chain of
+// table lookups in global memory. Either way the tile work below is the one
+// call site of stage_tile, so a domain computes the same bits alone or in
+// a batch.
 template <int STAGE>
-__global__ void __launch_bounds__(kWarps * 32, SWE_MIN_BLOCKS) stage_batch_kernel(const BatchTable tab) {
+__global__ void __launch_bounds__(kWarps * 32, SWE_MIN_BLOCKS)
+stage_batch_kernel(const BatchTable tab, const __grid_constant__ OneDomain one) {
     // the domain's arguments, staged once per block in shared memory (they
-    // are read uniformly by every thread; the table itself is in global memory)
+    // are read uniformly by every thread)
     __shared__ StageArgs<float> sa;
-    const int n_dom = *tab.n_domains;
-    const int total = n_dom > 0 ? tab.tile_start[n_dom] : 0;
+    const bool single = one.tiles > 0;
+    const int n_dom = single ? 1 : *tab.n_domains;
+    const int total = single ? one.tiles : (n_dom > 0 ? tab.tile_start[n_dom] : 0);
     int have = -1;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        int lo = 0, hi = n_dom;                 // tile_start[lo] <= t < tile_start[hi]
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (tab.tile_start[mid] <= t) lo = mid; else hi = mid;
+        int d = 0, first = 0, ntiles = one.tiles, rows = one.rows, strips = one.strips;
+        if (!single) {
+            int lo = 0, hi = n_dom;             // tile_start[lo] <= t < tile_start[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (tab.tile_start[mid] <= t) lo = mid; else hi = mid;
+            }
+            d = lo;
+            first = tab.tile_start[d];
+            ntiles = tab.tile_start[d + 1] - first;
+            rows = tab.rows[d];
+            strips = tab.grid_x[d];
         }
-        const int d = lo;
         if (d != have) {
-            const int *src = reinterpret_cast<const int *>(tab.args + d);
+            const int *src = single ? reinterpret_cast<const int *>(&one.args)
+                                    : reinterpret_cast<const int *>(tab.args + d);
             int *dst = reinterpret_cast<int *>(&sa);
             for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x)
                 dst[k] = src[k];
             __syncthreads();
             have = d;
         }
-        const int ntiles = tab.tile_start[d + 1] - tab.tile_start[d];
-        stage_tile<STAGE>(sa, t - tab.tile_start[d], tab.rows[d], tab.grid_x[d], ntiles,
-                          sa.comp[0] != nullptr);
+        stage_tile<STAGE>(sa, t - first, rows, strips, ntiles, sa.comp[0] != nullptr);
         __syncthreads();                        // shared scratch reused by the next tile
     }
 }
@@ -606,8 +627,19 @@ cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st) {
 
 cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st) {
     dim3 b(kWarps * 32);
-    if (stage == 1) stage_batch_kernel<1><<<blocks, b, 0, st>>>(tab);
-    else stage_batch_kernel<2><<<blocks, b, 0, st>>>(tab);
+    OneDomain none;
+    memset(&none, 0, sizeof none);
+    if (stage == 1) stage_batch_kernel<1><<<blocks, b, 0, st>>>(tab, none);
+    else stage_batch_kernel<2><<<blocks, b, 0, st>>>(tab, none);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st) {
+    dim3 b(kWarps * 32);
+    BatchTable tab;
+    memset(&tab, 0, sizeof tab);
+    if (stage == 1) stage_batch_kernel<1><<<one.tiles, b, 0, st>>>(tab, one);
+    else stage_batch_kernel<2><<<one.tiles, b, 0, st>>>(tab, one);
     return cudaGetLastError();
 }
 
