@@ -59,12 +59,11 @@ __device__ __forceinline__ void block_max_to(unsigned int *acc, float v, bool ha
 // corner bathymetry (Section 3.8), FP32: GB300's FP64 rate is a small
 // fraction of its FP32 rate, and the corners feed the FP32 stage kernels
 
-// dH = Hm - H*(i, j), H* the mean of the cell's four corners; the largest
-// |dH| goes to *acc when acc != NULL.
+// max |Hm - H*(i, j)| over the cells -> *acc, H* the mean of the cell's four
+// corners (the misfit of the final corners).
 __global__ void __launch_bounds__(kBX * kBY) residual_kernel(const float *Hm, long long pitch,
                                                              const float *Hc, long long cpitch,
-                                                             int nx, int ny, float *dH, long long wp,
-                                                             unsigned int *acc) {
+                                                             int nx, int ny, unsigned int *acc) {
     const int i = blockIdx.x * kBX + threadIdx.x % kBX;
     const int j = blockIdx.y * kBY + threadIdx.x / kBX;
     const bool in = i < nx && j < ny;
@@ -73,115 +72,160 @@ __global__ void __launch_bounds__(kBX * kBY) residual_kernel(const float *Hm, lo
         const float *c = Hc + (long long)j * cpitch + i;
         const float mid = 0.25f * (((c[0] + c[1]) + c[cpitch]) + c[cpitch + 1]);
         r = Hm[(long long)j * pitch + i] - mid;
-        dH[(long long)j * wp + i] = r;
     }
     block_max_to(acc, fabsf(r), in);
 }
 
-// eqn:recon_1: limited x and y slopes of field F per cell width; beyond the
-// edge a neighbour is the linear extrapolation 2 F_0 - F_1 (a single cell
-// along an axis has slope zero there).
-__global__ void __launch_bounds__(kBX * kBY) slope_kernel(const float *F, long long fp, int nx, int ny,
-                                                          float theta, float *sx, float *sy,
-                                                          long long wp) {
-    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
-    if (i >= nx || j >= ny) return;
-    const float *p = F + (long long)j * fp + i;
-    const float c = p[0];
-    float w, e, s, n;
-    if (nx == 1) { w = e = c; }
-    else {
-        w = i > 0 ? p[-1] : 2.f * c - p[1];
-        e = i < nx - 1 ? p[1] : 2.f * c - p[-1];
+// One iteration of the corner reconstruction (or, with X == NULL, the
+// initial guess) for a tile of kTY x kTX output corners, every intermediate
+// in shared memory, so an iteration reads Hm and the corners X and writes
+// the corners Y once (halo re-reads come from L2):
+//   A  the field F whose slopes are taken: Hm itself for the initial guess,
+//      else the residual dH = Hm - H*(i, j) of X (cells on a 3-cell halo);
+//   B  eqn:recon_1: the limited slopes of F (cells on a 2-cell halo; beyond
+//      an edge a value is linearly extrapolated);
+//   C  eqn:recon_2, eqn:recon_3: T = X + the mean of the planar estimates of
+//      the cells meeting at a corner (corners on a 1-corner halo);
+//   D  the smoothing pass Y = (1 - w) T + w (mean of T's 4 neighbours,
+//      extrapolated beyond an edge); the initial guess is T as it stands.
+// The misfit max|dH| of X and the largest change max|Y - X| go to misfit
+// and change.
+constexpr int kTX = 32, kTY = 16, kTileThreads = 256;
+
+__global__ void __launch_bounds__(kTileThreads) bathy_tile_kernel(const float *Hm, long long pitch, int nx,
+                                                                  int ny, const float *X, long long xp,
+                                                                  float *Y, long long yp, float theta,
+                                                                  float wgt, unsigned int *misfit,
+                                                                  unsigned int *change) {
+    __shared__ float D[kTY + 5][kTX + 5];
+    __shared__ float SX[kTY + 3][kTX + 3], SY[kTY + 3][kTX + 3];
+    __shared__ float T[kTY + 2][kTX + 2];
+    __shared__ float part[2][kTileThreads / 32];
+    const int I0 = blockIdx.x * kTX, J0 = blockIdx.y * kTY;
+    const bool init = X == nullptr;
+    float mis = 0.f, chg = 0.f;
+
+    // A: F on cells [J0-3, J0+kTY+2) x [I0-3, I0+kTX+2)
+    for (int k = threadIdx.x; k < (kTY + 5) * (kTX + 5); k += kTileThreads) {
+        const int a = k / (kTX + 5), b = k % (kTX + 5);
+        const int j = J0 - 3 + a, i = I0 - 3 + b;
+        float v = 0.f;
+        if (j >= 0 && j < ny && i >= 0 && i < nx) {
+            v = Hm[(long long)j * pitch + i];
+            if (!init) {
+                const float *c = X + (long long)j * xp + i;
+                v = v - 0.25f * (((c[0] + c[1]) + c[xp]) + c[xp + 1]);
+                if (a >= 3 && a < 3 + kTY && b >= 3 && b < 3 + kTX) mis = fmaxf(mis, fabsf(v));
+            }
+        }
+        D[a][b] = v;
     }
-    if (ny == 1) { s = n = c; }
-    else {
-        s = j > 0 ? p[-fp] : 2.f * c - p[fp];
-        n = j < ny - 1 ? p[fp] : 2.f * c - p[-fp];
+    __syncthreads();
+
+    // B: slopes of the cells [J0-2, J0+kTY+1) x [I0-2, I0+kTX+1)
+    for (int k = threadIdx.x; k < (kTY + 3) * (kTX + 3); k += kTileThreads) {
+        const int a = k / (kTX + 3), b = k % (kTX + 3);
+        const int j = J0 - 2 + a, i = I0 - 2 + b;
+        float sx = 0.f, sy = 0.f;
+        if (j >= 0 && j < ny && i >= 0 && i < nx) {
+            const float c = D[a + 1][b + 1];
+            float w = c, e = c, s = c, n = c;
+            if (nx > 1) {
+                w = i > 0 ? D[a + 1][b] : 2.f * c - D[a + 1][b + 2];
+                e = i < nx - 1 ? D[a + 1][b + 2] : 2.f * c - D[a + 1][b];
+            }
+            if (ny > 1) {
+                s = j > 0 ? D[a][b + 1] : 2.f * c - D[a + 2][b + 1];
+                n = j < ny - 1 ? D[a + 2][b + 1] : 2.f * c - D[a][b + 1];
+            }
+            const float bx = c - w, fx = e - c, by = c - s, fy = n - c;
+            sx = gminmod(theta * bx, 0.5f * (bx + fx), theta * fx);
+            sy = gminmod(theta * by, 0.5f * (by + fy), theta * fy);
+        }
+        SX[a][b] = sx;
+        SY[a][b] = sy;
     }
-    const float bx = c - w, fx = e - c, by = c - s, fy = n - c;
-    sx[(long long)j * wp + i] = gminmod(theta * bx, 0.5f * (bx + fx), theta * fx);
-    sy[(long long)j * wp + i] = gminmod(theta * by, 0.5f * (by + fy), theta * fy);
+    __syncthreads();
+
+    // C: T on the corners [J0-1, J0+kTY] x [I0-1, I0+kTX]
+    for (int k = threadIdx.x; k < (kTY + 2) * (kTX + 2); k += kTileThreads) {
+        const int a = k / (kTX + 2), b = k % (kTX + 2);
+        const int J = J0 - 1 + a, I = I0 - 1 + b;
+        float t = 0.f;
+        if (J >= 0 && J <= ny && I >= 0 && I <= nx) {
+            float total = 0.f;
+            int count = 0;
+            // the cells in the order: corner below-left of the centre (cell
+            // (J, I)), below-right (J, I-1), above-left (J-1, I), above-right (J-1, I-1)
+            for (int q = 0; q < 4; q++) {
+                const int gy = q < 2 ? -1 : 1, gx = (q & 1) ? 1 : -1;
+                const int j = gy < 0 ? J : J - 1, i = gx < 0 ? I : I - 1;
+                if (i < 0 || i >= nx || j < 0 || j >= ny) continue;
+                const int sa = j - J0 + 2, sb = i - I0 + 2;
+                total += (D[sa + 1][sb + 1] + 0.5f * gx * SX[sa][sb]) + 0.5f * gy * SY[sa][sb];
+                count++;
+            }
+            // 1, 2 or 4 estimates: the mean is an exact scaling
+            const float mean = total * (count == 4 ? 0.25f : (count == 2 ? 0.5f : 1.f));
+            t = init ? mean : X[(long long)J * xp + I] + mean;
+        }
+        T[a][b] = t;
+    }
+    __syncthreads();
+
+    // D: the tile's own corners
+    for (int k = threadIdx.x; k < kTY * kTX; k += kTileThreads) {
+        const int a = k / kTX, b = k % kTX;
+        const int J = J0 + a, I = I0 + b;
+        if (J > ny || I > nx) continue;
+        const float c = T[a + 1][b + 1];
+        float v = c;
+        if (!init) {
+            const float W = I > 0 ? T[a + 1][b] : 2.f * c - T[a + 1][b + 2];
+            const float E = I < nx ? T[a + 1][b + 2] : 2.f * c - T[a + 1][b];
+            const float S = J > 0 ? T[a][b + 1] : 2.f * c - T[a + 2][b + 1];
+            const float N = J < ny ? T[a + 2][b + 1] : 2.f * c - T[a][b + 1];
+            v = (1.f - wgt) * c + wgt * 0.25f * (((W + E) + S) + N);
+            chg = fmaxf(chg, fabsf(v - X[(long long)J * xp + I]));
+        }
+        Y[(long long)J * yp + I] = v;
+    }
+    if (init) return;                       // block-uniform
+    // block maxima of the misfit and the change, one atomic each
+    for (int o = 16; o > 0; o >>= 1) {
+        mis = fmaxf(mis, __shfl_xor_sync(0xffffffffu, mis, o));
+        chg = fmaxf(chg, __shfl_xor_sync(0xffffffffu, chg, o));
+    }
+    if ((threadIdx.x & 31) == 0) { part[0][threadIdx.x >> 5] = mis; part[1][threadIdx.x >> 5] = chg; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f, c = 0.f;
+        for (int w = 0; w < kTileThreads / 32; w++) { m = fmaxf(m, part[0][w]); c = fmaxf(c, part[1][w]); }
+        if (misfit) atomic_max_nonneg(misfit, m);
+        atomic_max_nonneg(change, c);
+    }
 }
 
-// eqn:recon_2 and eqn:recon_3: corner (J, I) is the mean of the planar
-// estimates of the (up to four) cells that meet there; out = base + mean
-// (base NULL: the mean alone).
-__global__ void __launch_bounds__(kBX * kBY) corner_kernel(const float *F, long long fp, const float *sx,
-                                                           const float *sy, long long wp, int nx, int ny,
-                                                           const float *base, long long cpitch,
-                                                           float *out, long long op) {
-    const int I = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int J = blockIdx.y * kBY + threadIdx.x / kBX;
-    if (I > nx || J > ny) return;
-    float total = 0.f;
-    int count = 0;
-    // the cells in the order: corner below-left of the centre (cell (J, I)),
-    // below-right (cell (J, I-1)), above-left (J-1, I), above-right (J-1, I-1)
-    for (int k = 0; k < 4; k++) {
-        const int gy = k < 2 ? -1 : 1, gx = (k & 1) ? 1 : -1;
-        const int j = gy < 0 ? J : J - 1, i = gx < 0 ? I : I - 1;
-        if (i < 0 || i >= nx || j < 0 || j >= ny) continue;
-        const long long c = (long long)j * wp + i;
-        const float est = (F[(long long)j * fp + i] + 0.5f * gx * sx[c]) + 0.5f * gy * sy[c];
-        total += est;
-        count++;
-    }
-    // 1, 2 or 4 estimates: the mean is an exact scaling
-    const float mean = total * (count == 4 ? 0.25f : (count == 2 ? 0.5f : 1.f));
-    out[(long long)J * op + I] = base ? base[(long long)J * cpitch + I] + mean : mean;
-}
-
-// Hc := (1 - w) T + w (mean of T's four neighbour corners, linearly
-// extrapolated beyond the edge); the largest |Hc_new - Hc_old| -> *acc.
-__global__ void __launch_bounds__(kBX * kBY) smooth_kernel(const float *T, long long tp, float *Hc,
-                                                           long long cpitch, int ncx, int ncy, float wgt,
-                                                           unsigned int *acc) {
-    const int I = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int J = blockIdx.y * kBY + threadIdx.x / kBX;
-    const bool in = I < ncx && J < ncy;
-    float change = 0.f;
-    if (in) {
-        const float *p = T + (long long)J * tp + I;
-        const float c = p[0];
-        const float W = I > 0 ? p[-1] : 2.f * c - p[1];
-        const float E = I < ncx - 1 ? p[1] : 2.f * c - p[-1];
-        const float S = J > 0 ? p[-tp] : 2.f * c - p[tp];
-        const float N = J < ncy - 1 ? p[tp] : 2.f * c - p[-tp];
-        const float v = (1.f - wgt) * c + wgt * 0.25f * (((W + E) + S) + N);
-        float *h = Hc + (long long)J * cpitch + I;
-        change = fabsf(v - *h);
-        *h = v;
-    }
-    block_max_to(acc, change, in);
-}
-
+// Work area: one corner plane (the iterations alternate between it and the
+// caller's corners, ending in the caller's) and the per-iteration statistics.
 struct BathyWork {
-    float *dH, *sx, *sy, *tmp;
+    float *corners;
     unsigned int *stats;
-    long long wp, tp;
+    long long tp;
 };
 
 BathyWork bathy_layout(void *work, int nx, int ny) {
     BathyWork w;
-    w.wp = round_up(nx, 32);
     w.tp = round_up((long long)nx + 1, 32);
     char *p = static_cast<char *>(work);
-    const size_t plane = (size_t)round_up((long long)w.wp * ny * 4, 256);
-    w.dH = reinterpret_cast<float *>(p);
-    w.sx = reinterpret_cast<float *>(p + plane);
-    w.sy = reinterpret_cast<float *>(p + 2 * plane);
-    w.tmp = reinterpret_cast<float *>(p + 3 * plane);
-    const size_t cplane = (size_t)round_up((long long)w.tp * (ny + 1) * 4, 256);
-    w.stats = reinterpret_cast<unsigned int *>(p + 3 * plane + cplane);
+    w.corners = reinterpret_cast<float *>(p);
+    w.stats = reinterpret_cast<unsigned int *>(p + round_up(w.tp * (ny + 1) * 4, 256));
     return w;
 }
 
 size_t bathy_bytes(int nx, int ny) {
-    const long long wp = round_up(nx, 32), tp = round_up((long long)nx + 1, 32);
-    return (size_t)(3 * round_up(wp * ny * 4, 256) + round_up(tp * (ny + 1) * 4, 256)) +
-           2 * kMaxIter * sizeof(unsigned int);
+    const long long tp = round_up((long long)nx + 1, 32);
+    return (size_t)round_up(tp * (ny + 1) * 4, 256) + 2 * kMaxIter * sizeof(unsigned int);
 }
 
 // ---------------------------------------------------------------------------
@@ -348,25 +392,27 @@ int swe_bathymetry_reconstruct(const float *Hm, long long pitch, int nx, int ny,
     if ((reinterpret_cast<uintptr_t>(work) & 255u) != 0) return SWE_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const BathyWork w = bathy_layout(work, nx, ny);
-    const dim3 blk(kBX * kBY), gc = grid_for(nx, ny), gk = grid_for(nx + 1, ny + 1);
+    const dim3 tiles((unsigned)((nx + 1 + kTX - 1) / kTX), (unsigned)((ny + 1 + kTY - 1) / kTY));
     const float th = (float)theta, sm = (float)smooth;
     cudaError_t e = cudaMemsetAsync(w.stats, 0, 2 * kMaxIter * sizeof(unsigned int), st);
     if (e != cudaSuccess) return prep_fail(e);
-    // initial guess from the cell averages themselves
-    slope_kernel<<<gc, blk, 0, st>>>(Hm, pitch, nx, ny, th, w.sx, w.sy, w.wp);
-    corner_kernel<<<gk, blk, 0, st>>>(Hm, pitch, w.sx, w.sy, w.wp, nx, ny, nullptr, 0, Hc, cpitch);
+    // corners after k iterations live in plane (n_iter - k) % 2: 0 the caller's, 1 the work area's
+    float *plane[2] = {Hc, w.corners};
+    const long long pp[2] = {cpitch, w.tp};
+    int cur = n_iter % 2;
+    bathy_tile_kernel<<<tiles, kTileThreads, 0, st>>>(Hm, pitch, nx, ny, nullptr, 0, plane[cur], pp[cur], th,
+                                                      sm, nullptr, nullptr);
     for (int k = 0; k < n_iter; k++) {
-        // misfit of the previous iteration's corners (none for the initial guess)
-        residual_kernel<<<gc, blk, 0, st>>>(Hm, pitch, Hc, cpitch, nx, ny, w.dH, w.wp,
-                                            k > 0 ? w.stats + 2 * (k - 1) : nullptr);
-        slope_kernel<<<gc, blk, 0, st>>>(w.dH, w.wp, nx, ny, th, w.sx, w.sy, w.wp);
-        corner_kernel<<<gk, blk, 0, st>>>(w.dH, w.wp, w.sx, w.sy, w.wp, nx, ny, Hc, cpitch, w.tmp, w.tp);
-        smooth_kernel<<<gk, blk, 0, st>>>(w.tmp, w.tp, Hc, cpitch, nx + 1, ny + 1, sm,
-                                          w.stats + 2 * k + 1);
+        // the misfit of the previous iteration's corners (none for the initial guess)
+        bathy_tile_kernel<<<tiles, kTileThreads, 0, st>>>(Hm, pitch, nx, ny, plane[cur], pp[cur],
+                                                          plane[cur ^ 1], pp[cur ^ 1], th, sm,
+                                                          k > 0 ? w.stats + 2 * (k - 1) : nullptr,
+                                                          w.stats + 2 * k + 1);
+        cur ^= 1;
     }
     if (n_iter > 0)
-        residual_kernel<<<gc, blk, 0, st>>>(Hm, pitch, Hc, cpitch, nx, ny, w.dH, w.wp,
-                                            w.stats + 2 * (n_iter - 1));
+        residual_kernel<<<grid_for(nx, ny), kBX * kBY, 0, st>>>(Hm, pitch, Hc, cpitch, nx, ny,
+                                                                w.stats + 2 * (n_iter - 1));
     if ((e = cudaGetLastError()) != cudaSuccess) return prep_fail(e);
     if (stats && n_iter > 0) {
         unsigned int bits[2 * kMaxIter];
