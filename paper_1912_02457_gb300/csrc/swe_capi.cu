@@ -1,5 +1,6 @@
 // swe_capi.cu -- host implementation of the libswe C ABI (include/swe.h).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -36,6 +37,9 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 }  // namespace
 
 int swe::record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+swe::TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+swe::TraceRange::~TraceRange() { nvtxRangePop(); }
 
 struct swe_domain {
     int nx = 0, ny = 0, prec = 0;
@@ -364,6 +368,7 @@ void swe_default_params(swe_params *p) {
 }
 
 int swe_create_domain(const swe_domain_desc *d, const swe_params *p, void *stream, swe_handle *out) {
+    swe::TraceRange trace("swe_create_domain");
     if (!out) return SWE_ERR_INVALID_ARG;
     *out = nullptr;
     int rc = validate(d, p);
@@ -383,6 +388,7 @@ int swe_create_domain(const swe_domain_desc *d, const swe_params *p, void *strea
 
 int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times, const float *frames,
                     int n1, int n2) {
+    swe::TraceRange trace("swe_set_forcing");
     if (!h || n_frames < 0 || (n_frames > 0 && (!times || !frames))) return SWE_ERR_INVALID_ARG;
     if (kind != SWE_FORCING_WIND && kind != SWE_FORCING_BOUNDARY) return SWE_ERR_INVALID_ARG;
     if (n_frames > 0 && (n1 < 1 || n2 < 1)) return SWE_ERR_INVALID_ARG;
@@ -461,6 +467,7 @@ int ensure_graph(swe_handle h) {
 }  // namespace
 
 int swe_step(swe_handle h, int n_steps) {
+    swe::TraceRange trace("swe_step");
     int rc = step_check(h, n_steps);
     if (rc) return rc;
     const int parts = h->parts();
@@ -489,6 +496,7 @@ const char *swe_launch_name(swe_handle h, int part) {
 }
 
 int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
+    swe::TraceRange trace("swe_step_profiled");
     int rc = step_check(h, n_steps);
     if (rc) return rc;
     const int parts = h->parts();
@@ -513,6 +521,7 @@ int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
 }
 
 int swe_read_state(swe_handle h, int field, void *dst, int dst_is_device) {
+    swe::TraceRange trace("swe_read_state");
     if (!h || !dst) return SWE_ERR_INVALID_ARG;
     const void *src = nullptr;
     if (field >= SWE_COMP_ETA && field <= SWE_COMP_HV) {
@@ -552,6 +561,7 @@ int swe_set_end_time(swe_handle h, double t_end) {
 }
 
 int swe_write_state(swe_handle h, int field, const void *src, int src_is_device) {
+    swe::TraceRange trace("swe_write_state");
     if (!h || !src) return SWE_ERR_INVALID_ARG;
     if (field >= SWE_ETA && field <= SWE_HV) {
         for (int b = 0; b < 2; b++) {
@@ -598,6 +608,7 @@ int swe_get_info(swe_handle h, swe_info *out) {
 }
 
 int swe_diagnostics(swe_handle h, double out[2]) {
+    swe::TraceRange trace("swe_diagnostics");
     if (!h || !out) return SWE_ERR_INVALID_ARG;
     cudaError_t e;
     if (h->prec == SWE_F64) e = swe::launch_diagnostics(make_args<double>(h), h->diag_partials, h->diag_out, h->stream);
@@ -804,6 +815,7 @@ int swe_batch_set_rows(swe_batch_handle b, int rows) {
 int swe_batch_rows(swe_batch_handle b) { return b ? b->rows_choice : SWE_ERR_INVALID_ARG; }
 
 int swe_batch_step(swe_batch_handle b, int n_steps) {
+    swe::TraceRange trace("swe_batch_step");
     if (!b || n_steps < 0) return SWE_ERR_INVALID_ARG;
     if (b->doms.empty() || n_steps == 0) return SWE_OK;
     int rc;
@@ -829,6 +841,7 @@ int swe_batch_step(swe_batch_handle b, int n_steps) {
 }
 
 int swe_batch_step_serial(swe_batch_handle b, int n_steps) {
+    swe::TraceRange trace("swe_batch_step_serial");
     if (!b || n_steps < 0) return SWE_ERR_INVALID_ARG;
     for (int s = 0; s < n_steps; s++)
         for (swe_handle d : b->doms)

@@ -42,4 +42,14 @@ int diag_blocks(int nx, int ny);
 // Record e for swe_last_cuda_error and return SWE_ERR_CUDA (swe_capi.cu).
 int record_cuda_error(cudaError_t e);
 
+// An NVTX range over a host entry point (a no-op unless a profiler that
+// collects NVTX is attached): the library's calls show up by name in nsys /
+// ncu timelines beside the kernels they enqueue.
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 }  // namespace swe

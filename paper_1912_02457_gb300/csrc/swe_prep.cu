@@ -384,6 +384,7 @@ size_t swe_bathymetry_work_bytes(int nx, int ny) {
 int swe_bathymetry_reconstruct(const float *Hm, long long pitch, int nx, int ny, float *Hc,
                                long long cpitch, void *work, int n_iter, double theta,
                                double smooth, double *stats, void *stream) {
+    swe::TraceRange trace("swe_bathymetry_reconstruct");
     if (!Hm || !Hc || !work || nx < 1 || ny < 1 || pitch < nx || cpitch < (long long)nx + 1)
         return SWE_ERR_INVALID_ARG;
     if (n_iter < 0 || n_iter > kMaxIter || !(theta >= 1.0 && theta <= 2.0) ||
@@ -431,6 +432,7 @@ int swe_bathymetry_reconstruct(const float *Hm, long long pitch, int nx, int ny,
 int swe_land_erode(const unsigned char *land, const float *eta, const float *Hm,
                    long long pitch, int nx, int ny, double land_depth,
                    unsigned char *land_out, float *eta_out, float *Hm_out, void *stream) {
+    swe::TraceRange trace("swe_land_erode");
     if (!land || !eta || !Hm || !land_out || !eta_out || !Hm_out || nx < 1 || ny < 1 || pitch < nx)
         return SWE_ERR_INVALID_ARG;
     if ((const void *)land_out == (const void *)land || eta_out == eta || Hm_out == Hm)
@@ -446,6 +448,7 @@ int swe_refine2(const float *eta, const float *hu, const float *hv, long long pi
                 const float *H, long long cpitch, int nx, int ny, double theta,
                 float *eta_f, float *hu_f, float *hv_f, long long fpitch, float *H_f,
                 long long fcpitch, void *stream) {
+    swe::TraceRange trace("swe_refine2");
     if (!eta || !hu || !hv || !H || !eta_f || !hu_f || !hv_f || !H_f) return SWE_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536 || pitch < nx || cpitch < (long long)nx + 1)
         return SWE_ERR_INVALID_ARG;
@@ -465,6 +468,7 @@ int swe_refine2(const float *eta, const float *hu, const float *hv, long long pi
 int swe_coarsen2(const float *eta_f, const float *hu_f, const float *hv_f, long long fpitch,
                  const float *H_f, long long fcpitch, int nx, int ny, float *eta, float *hu,
                  float *hv, long long pitch, float *H, long long cpitch, void *stream) {
+    swe::TraceRange trace("swe_coarsen2");
     if (!eta_f || !hu_f || !hv_f || !H_f || !eta || !hu || !hv || !H) return SWE_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536 || pitch < nx || cpitch < (long long)nx + 1)
         return SWE_ERR_INVALID_ARG;
