@@ -147,13 +147,17 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources that define the stage kernels (their per-cell arithmetic, their
+# arguments and their launch shape); host-side files do not change them
+STAGE_KERNEL_SOURCES = ("swe_device.cuh", "swe_internal.h", "swe_stage_fast.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1912_02457_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(fh.read())
+    for name in STAGE_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
