@@ -335,13 +335,22 @@ def run_ours(args):
             import oracle
             o = oracle.Oracle(wl)
             n_cpu = args.cpu_steps
+            cores = oracle.num_threads()
             c0 = time.perf_counter()
             o.run(n_cpu)
             cel = time.perf_counter() - c0
-            cpu = {"value": cells * n_cpu / cel, "unit": UNIT, "cores": oracle.num_threads(),
+            # and on one core, a shorter sample of the same run
+            n1 = max(2, n_cpu // 8)
+            oracle.set_threads(1)
+            c1 = time.perf_counter()
+            o.run(n1)
+            cel1 = time.perf_counter() - c1
+            oracle.set_threads(cores)
+            cpu = {"value": cells * n_cpu / cel, "unit": UNIT, "cores": cores,
                    "kind": "oracle",
                    "sample": f"FP64 oracle, first {n_cpu} steps of the same 1024x1024 workload "
-                             f"({cel:.1f} s)"}
+                             f"({cel:.1f} s); one core: first {n1} steps ({cel1:.1f} s)",
+                   "single_core_value": cells * n1 / cel1}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -470,6 +479,14 @@ def run_ensemble(args):
            "batched_value": cells * n / t_batched, "serial_value": cells * n / t_serial,
            "speedup_vs_one_by_one": t_serial / t_batched, "tile_rows": b.rows(),
            "batched_ms_per_step": 1e3 * t_batched / n, "serial_ms_per_step": 1e3 * t_serial / n}
+    # the batched step against the HBM roofline: the algorithmic bytes of
+    # both stages of every domain over the time of one batched step
+    ab = sum(algorithmic_bytes(w, "f32_kahan")["stage1"] + algorithmic_bytes(w, "f32_kahan")["stage2"]
+             for w in wls)
+    peak, peak_src = measured_hbm_peak()
+    res["batched_hbm"] = {"algorithmic_bytes_per_step": ab,
+                          "achieved_gbs": ab / (t_batched / n) / 1e9,
+                          "frac": ab / (t_batched / n) / 1e9 / peak, "peak": peak, "peak_source": peak_src}
     b.close()
     for d in doms:
         d.close()

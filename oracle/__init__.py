@@ -88,6 +88,8 @@ def lib():
             L.orc_face_flux.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
                                         C.c_int, _dp]
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_threads.restype = None
+            L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
 
@@ -217,3 +219,8 @@ def face_flux(left, right, Hf, dir, g=9.81, kappa=1e-2):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_threads(int(n))

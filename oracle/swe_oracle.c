@@ -954,6 +954,18 @@ void orc_diagnostics(const orc_domain *d, const double *eta, const double *hu,
     *energy = e * d->dx * d->dy;
 }
 
+/* Threads of the parallel loops from now on (the CPU baseline also times
+ * the oracle on one core). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
