@@ -38,7 +38,10 @@ typedef enum {
     SWE_ERR_OOM = -2,          /* device or host allocation failed */
     SWE_ERR_CUDA = -3,         /* a CUDA call failed; see swe_last_cuda_error */
     SWE_ERR_NUMERIC = -4,      /* non-finite state or time step (sticky) */
-    SWE_ERR_UNSUPPORTED = -5   /* option not built into this library */
+    SWE_ERR_UNSUPPORTED = -5,  /* option not built into this library */
+    SWE_ERR_BOUNDS = -6        /* a kernel access outside its buffer was caught
+                                  and skipped (bounds-checked debug builds only;
+                                  sticky; swe_info.error_cell = source line) */
 } swe_status;
 
 typedef enum {

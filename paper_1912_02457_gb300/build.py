@@ -37,29 +37,37 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale(extra_flags):
-    if not os.path.exists(LIB):
+def _paths(variant):
+    """Output folder and library of a build variant ("" is the product)."""
+    out = os.path.join(OUT_DIR, variant) if variant else OUT_DIR
+    return out, os.path.join(out, "libswe.so")
+
+
+def _stale(extra_flags, variant=""):
+    out_dir, lib = _paths(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
     deps += glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
-    stamp = os.path.join(OUT_DIR, "flags.txt")
+    stamp = os.path.join(out_dir, "flags.txt")
     want = " ".join(extra_flags)
     if not os.path.exists(stamp) or open(stamp).read() != want:
         return True
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variant: str = "") -> str:
+    out_dir, lib = _paths(variant)
+    os.makedirs(out_dir, exist_ok=True)
     extra_flags = list(extra_flags)
-    if not force and not _stale(extra_flags):
-        return LIB
+    if not force and not _stale(extra_flags, variant):
+        return lib
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []),
                *extra_flags, "-c", src, "-o", obj]
         if verbose:
@@ -73,15 +81,24 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(os.path.join(OUT_DIR, "flags.txt"), "w") as fh:
+    os.replace(tmp, lib)
+    with open(os.path.join(out_dir, "flags.txt"), "w") as fh:
         fh.write(" ".join(extra_flags))
-    return LIB
+    return lib
+
+
+def build_debug(force: bool = False) -> str:
+    """The bounds-checked variant (_build/debug/libswe.so): every global
+    access of the FP32 stage kernels checks its offset against the extent of
+    its buffer; a violation is skipped and reported as SWE_ERR_BOUNDS with
+    the source line in swe_info.error_cell. A test tool, slower than the
+    product."""
+    return build(force=force, extra_flags=["-DSWE_DEBUG_BOUNDS"], variant="debug")
 
 
 if __name__ == "__main__":

@@ -3,6 +3,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -165,6 +166,17 @@ StageArgs<T> make_args(const swe_domain *d) {
     }
     a.ctl = d->ctl;
     a.edge = d->edge;
+    a.n_plane = d->pitch * d->ny;
+    a.n_corner = d->cpitch * (d->ny + 1);
+    a.n_edge = d->edge ? swe::edge_floats(d->nx, d->ny) : 0;
+    a.n_bnd = (long long)d->bnd_n * 12 * (d->bnd_n1 + d->bnd_n2);
+    a.n_wind = (long long)d->wind_n * 2 * d->wind_n1 * d->wind_n2;
+#ifdef SWE_DEBUG_BOUNDS
+    // test knob of the bounds-checked build: declare the last rows of every
+    // state plane out of bounds (the allocation itself is untouched, so an
+    // access the checks let through still lands inside it)
+    if (const char *v = getenv("SWE_DEBUG_SHRINK_PLANE_ROWS")) a.n_plane -= atoll(v) * d->pitch;
+#endif
     a.clk.courant = d->p.courant;
     a.clk.dt_fixed = d->p.dt_fixed;
     a.clk.dt_every = d->p.dt_update_every < 1 ? 1 : d->p.dt_update_every;
@@ -602,7 +614,7 @@ int swe_get_info(swe_handle h, swe_info *out) {
     out->t_end = c.t_end;
     if (c.err != 0) {
         h->sticky_numeric = true;
-        return SWE_ERR_NUMERIC;
+        return c.err == swe::ERR_BOUNDS ? SWE_ERR_BOUNDS : SWE_ERR_NUMERIC;
     }
     return SWE_OK;
 }

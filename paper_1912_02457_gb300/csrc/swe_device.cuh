@@ -246,6 +246,25 @@ __device__ __forceinline__ void axis_pos_f(int k, int n, int nb, int &k0, int &k
 // Wind stress at cell (i, j) at the stage time (Section 3.5): uniform
 // frames use the stress the clock kernel computed in FP64; gridded frames
 // are sampled bilinearly at the cell centre and lerped in time here.
+// Bounds checks of the debug builds (-DSWE_DEBUG_BOUNDS): SWE_CHECK(a, off,
+// n) is true when 0 <= off < n; otherwise it records SWE_ERR_BOUNDS (with
+// the source line in err_cell) and the caller skips the access. In product
+// builds it is the constant true and costs nothing.
+#ifdef SWE_DEBUG_BOUNDS
+static __device__ __noinline__ void flag_bounds(StepCtl *ctl, int line) {
+    atomicExch(&ctl->err, (int)ERR_BOUNDS);
+    atomicCAS(&ctl->err_cell, -1, line);
+}
+__device__ __forceinline__ bool in_bounds(StepCtl *ctl, long long off, long long n, int line) {
+    if (off >= 0 && off < n) return true;
+    flag_bounds(ctl, line);
+    return false;
+}
+#define SWE_CHECK(a, off, n) ::swe::in_bounds((a).ctl, (long long)(off), (long long)(n), __LINE__)
+#else
+#define SWE_CHECK(a, off, n) true
+#endif
+
 template <typename T>
 __device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int stage,
                                         T rho_ratio, T &tx, T &ty) {
@@ -263,14 +282,15 @@ __device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int
     int fk = a.ctl->wk[stage];
     float s = (float)a.ctl->ws[stage];
     long long fs = 2LL * F.n1 * F.n2;
-    const float *A = F.frames + fk * fs;
-    const float *B = F.n > 1 ? A + fs : A;
+    const long long oa = fk * fs, ob = F.n > 1 ? oa + fs : oa;
+    auto A = [&](long long o) { return SWE_CHECK(a, oa + o, a.n_wind) ? F.frames[oa + o] : 0.f; };
+    auto B = [&](long long o) { return SWE_CHECK(a, ob + o, a.n_wind) ? F.frames[ob + o] : 0.f; };
     float W[2];
     for (int c = 0; c < 2; c++) {
-        float a0 = (1.f - wx) * A[(y0 * F.n1 + x0) * 2 + c] + wx * A[(y0 * F.n1 + x1) * 2 + c];
-        float a1 = (1.f - wx) * A[(y1 * F.n1 + x0) * 2 + c] + wx * A[(y1 * F.n1 + x1) * 2 + c];
-        float b0 = (1.f - wx) * B[(y0 * F.n1 + x0) * 2 + c] + wx * B[(y0 * F.n1 + x1) * 2 + c];
-        float b1 = (1.f - wx) * B[(y1 * F.n1 + x0) * 2 + c] + wx * B[(y1 * F.n1 + x1) * 2 + c];
+        float a0 = (1.f - wx) * A((y0 * F.n1 + x0) * 2 + c) + wx * A((y0 * F.n1 + x1) * 2 + c);
+        float a1 = (1.f - wx) * A((y1 * F.n1 + x0) * 2 + c) + wx * A((y1 * F.n1 + x1) * 2 + c);
+        float b0 = (1.f - wx) * B((y0 * F.n1 + x0) * 2 + c) + wx * B((y0 * F.n1 + x1) * 2 + c);
+        float b1 = (1.f - wx) * B((y1 * F.n1 + x0) * 2 + c) + wx * B((y1 * F.n1 + x1) * 2 + c);
         W[c] = (1.f - s) * ((1.f - wy) * a0 + wy * a1) + s * ((1.f - wy) * b0 + wy * b1);
     }
     wind_stress<T>(T(W[0]), T(W[1]), rho_ratio, tx, ty);

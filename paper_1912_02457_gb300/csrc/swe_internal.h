@@ -11,7 +11,7 @@ constexpr int kMaxFrs = 32;          // deepest flow-relaxation zone supported
 constexpr float kLand = 3.40282346638528859812e+38f;  // FLT_MAX corner marker
 enum { EDGE_S = 0, EDGE_N = 1, EDGE_W = 2, EDGE_E = 3 };
 enum { BC_WALL = 0, BC_NESTED = 1, BC_PERIODIC = 2 };
-enum { ERR_NONE = 0, ERR_NUMERIC = -4 };
+enum { ERR_NONE = 0, ERR_NUMERIC = -4, ERR_BOUNDS = -6 };
 
 // Device-resident clock of one domain. The stage kernels read dt and the
 // forcing brackets from here and the end-of-step reduction writes the next
@@ -81,6 +81,8 @@ struct StageArgs {
     // 12 nx + 6 ny; within an edge of length n, value v of ring r at
     // position k sits at (3 r + v) n + k.
     float *edge;
+    // elements of each buffer (checked by the bounds-checked debug builds)
+    long long n_plane, n_corner, n_edge, n_bnd, n_wind;
 };
 
 // A single FP32 domain handed to the persistent stage kernel with the launch

@@ -62,12 +62,13 @@ __device__ __forceinline__ void bnd_state_f(const StageArgs<float> &a, int e, in
     int fk = a.ctl->bk[stage];
     float s = a.ctl->bs_f[stage];
     long long fs = 12LL * (F.n1 + F.n2);
-    const float *A = F.frames + (long long)fk * fs + off + (long long)(r * 3) * nb;
-    const float *B = F.n > 1 ? A + fs : A;
+    const long long oa = (long long)fk * fs + off + (long long)(r * 3) * nb;
+    const long long ob = F.n > 1 ? oa + fs : oa;
+    auto ld = [&](long long o) { return SWE_CHECK(a, o, a.n_bnd) ? F.frames[o] : 0.f; };
     float out[3];
     for (int v = 0; v < 3; v++) {
-        float va = (1.f - w) * A[v * nb + k0] + w * A[v * nb + k1];
-        float vb = (1.f - w) * B[v * nb + k0] + w * B[v * nb + k1];
+        float va = (1.f - w) * ld(oa + v * nb + k0) + w * ld(oa + v * nb + k1);
+        float vb = (1.f - w) * ld(ob + v * nb + k0) + w * ld(ob + v * nb + k1);
         out[v] = (1.f - s) * va + s * vb;
     }
     v0 = out[0]; v1 = out[1]; v2 = out[2];
@@ -87,7 +88,7 @@ __device__ void edge_fill(const StageArgs<float> &a, int slot, int stage, int id
     if (!a.edge || a.bnd.n <= 0) return;
     const int nx = a.nx, ny = a.ny;
     const int total = 4 * (nx + ny);
-    float *L = a.edge + (long long)slot * 12 * (nx + ny);
+    const long long base = (long long)slot * 12 * (nx + ny);
     for (; idx < total; idx += stride) {
         int e, q = idx;
         if (q < 2 * nx) e = EDGE_S;
@@ -99,8 +100,10 @@ __device__ void edge_fill(const StageArgs<float> &a, int slot, int stage, int id
         const int r = q / n, k = q - r * n;
         float v0, v1, v2;
         bnd_state_f(a, e, r, k, stage, v0, v1, v2);
-        float *o = L + edge_base(e, nx, ny) + 3 * r * n + k;
-        o[0] = v0; o[n] = v1; o[2 * n] = v2;
+        const long long o = base + edge_base(e, nx, ny) + 3 * r * n + k;
+        if (SWE_CHECK(a, o, a.n_edge) && SWE_CHECK(a, o + 2 * n, a.n_edge)) {
+            a.edge[o] = v0; a.edge[o + n] = v1; a.edge[o + 2 * n] = v2;
+        }
     }
 }
 
@@ -141,20 +144,30 @@ __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, i
     }
     // offsets fit in 32 bits (checked when the domain is created)
     const int cp = (int)a.cpitch;
-    const float *H = a.H + (sj * cp + si);
-    w.c00 = __ldg(H); w.c10 = __ldg(H + 1); w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
+    const int h0 = sj * cp + si;
     const int s = sj * (int)a.pitch + si;
-    w.f = a.f ? __ldg(a.f + s) : a.f_const;
-    w.th = a.th ? __ldg(a.th + s) : a.th_const;
     // an interior cell reads the state planes; a ghost reads its edge's values,
     // stage 1 at the time level of Q^n (slot par), stage 2 at the next one
+    int pe = 0, ne = 0;
+    if (e >= 0) {
+        ne = e < 2 ? nx : ny;
+        pe = (STAGE == 1 ? par : par ^ 1) * 12 * (nx + ny) + edge_base(e, nx, ny) + 3 * ring * ne +
+             (e >= EDGE_W ? r : i);
+    }
+    if (!(SWE_CHECK(a, h0, a.n_corner) && SWE_CHECK(a, h0 + cp + 1, a.n_corner) && SWE_CHECK(a, s, a.n_plane) &&
+          (e < 0 || (SWE_CHECK(a, pe, a.n_edge) && SWE_CHECK(a, pe + 2 * ne, a.n_edge))))) {
+        w.c00 = w.c10 = w.c01 = w.c11 = kLand;
+        return;
+    }
+    const float *H = a.H + h0;
+    w.c00 = __ldg(H); w.c10 = __ldg(H + 1); w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
+    w.f = a.f ? __ldg(a.f + s) : a.f_const;
+    w.th = a.th ? __ldg(a.th + s) : a.th_const;
     const float *p0 = a.q[par][0] + s, *p1 = a.q[par][1] + s, *p2 = a.q[par][2] + s;
     if (e >= 0) {
-        const int n = e < 2 ? nx : ny;
-        const int slot = STAGE == 1 ? par : par ^ 1;
-        p0 = a.edge + slot * 12 * (nx + ny) + edge_base(e, nx, ny) + 3 * ring * n + (e >= EDGE_W ? r : i);
-        p1 = p0 + n;
-        p2 = p1 + n;
+        p0 = a.edge + pe;
+        p1 = p0 + ne;
+        p2 = p1 + ne;
     }
     w.q0 = __ldg(p0); w.q1 = __ldg(p1); w.q2 = __ldg(p2);
     if (STAGE == 2) {
@@ -277,8 +290,8 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
 
     // the loads of the output row are issued first so that their latency
     // hides behind the x and y work of this iteration
-    const bool write = OUT && k.out_lane && !w.A.land;
     const int s_out = (r - 2) * (int)a.pitch + k.i;
+    const bool write = OUT && k.out_lane && !w.A.land && SWE_CHECK(a, s_out, a.n_plane);
     float oq[3] = {0.f, 0.f, 0.f}, oD[3] = {0.f, 0.f, 0.f}, oc[3] = {0.f, 0.f, 0.f};
     if (STAGE == 2 && write) {
         for (int v = 0; v < 3; v++) {
@@ -396,8 +409,9 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
                 float al = a.frs_alpha_f[d];
                 // external state at the new time level, ring 0
                 const int n = e < 2 ? a.nx : a.ny;
-                const float *E = a.edge + (par ^ 1) * 12 * (a.nx + a.ny) + edge_base(e, a.nx, a.ny) +
-                                 (e >= EDGE_W ? ro : k.i);
+                const int pe = (par ^ 1) * 12 * (a.nx + a.ny) + edge_base(e, a.nx, a.ny) + (e >= EDGE_W ? ro : k.i);
+                if (!(SWE_CHECK(a, pe, a.n_edge) && SWE_CHECK(a, pe + 2 * n, a.n_edge))) continue;
+                const float *E = a.edge + pe;
                 const float x0 = __ldg(E), x1 = __ldg(E + n), x2 = __ldg(E + 2 * n);
                 if (KAHAN) {
                     kahan_add(q0, c0, al * (x0 - q0));
