@@ -139,6 +139,23 @@ def whole_job_rate(units_per_rank: float, seconds: float, world_size: int) -> fl
     return units_per_rank * world_size / max_over_ranks(seconds)
 
 
+def issue_roofline(kernel: str, avg_launch_ms: float, clocks: dict):
+    """The dominant kernel against the GPU's instruction-issue rate (the
+    stage kernels are bound by issue, not by HBM): warp instructions per
+    launch (ncu) over the measured launch time, against SMs x schedulers x
+    the median SM clock sampled during the timed region."""
+    inst = committed_counter("warp_instructions", kernel)
+    mhz = clocks.get("sm_mhz") if isinstance(clocks, dict) else None
+    if inst is None or not mhz:
+        return None
+    peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6
+    achieved = inst / (avg_launch_ms * 1e-3)
+    return {"bound": "issue", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": inst,
+            "peak_source": f"{SMS} SMs x {SCHEDULERS_PER_SM} schedulers x {mhz:.0f} MHz (sampled)"}
+
+
 def measured_hbm_peak():
     try:
         with open(PEAKS_FILE) as fh:
@@ -161,9 +178,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def committed_counter(name: str, kernel: str):
+    """A per-launch counter of `kernel` (dram_bytes, warp_instructions) from
+    the committed ncu summary, if it was taken on the current kernel sources;
+    else None."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -172,9 +190,18 @@ def committed_traffic(kernel: str):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_sources_sha256_16") != kernel_source_hash():
             return None
-        return float(kv[f"dram_bytes_per_launch_{kernel}"])
+        return float(kv[f"{name}_per_launch_{kernel}"])
     except Exception:
         return None
+
+
+def committed_traffic(kernel: str):
+    return committed_counter("dram_bytes", kernel)
+
+
+# instruction issue of the whole GPU: 152 SMs x 4 schedulers x one warp
+# instruction per cycle at the SM clock
+SMS, SCHEDULERS_PER_SM = 152, 4
 
 
 def algorithmic_bytes(wl, precision):
@@ -365,6 +392,7 @@ def run_ours(args):
                          "avg_launch_ms": float(kern_avg[dom_k])},
             "kernels": {p: {"avg_ms": float(kern_avg[i]), "share": float(kern_tot[i] / kern_tot.sum())}
                         for i, p in enumerate(parts)},
+            "issue_roofline": issue_roofline(name, float(kern_avg[dom_k]), clocks.summary()),
             "back_to_back_ms_per_step": b2b_ms,
             "back_to_back_value": cells / (b2b_ms * 1e-3),
             "cpu_baseline": cpu,
