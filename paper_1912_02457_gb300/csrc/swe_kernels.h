@@ -24,7 +24,8 @@ cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long
 
 // FP32 sliding-window stage kernels (swe_stage_fast.cu): stage 1, then
 // stage 2 with the fused CFL reduction and clock update. A single domain
-// runs through the same kernel as a batch, with a one-entry tile table.
+// runs through the same kernel as a batch, its arguments in the launch's
+// parameter space.
 int fast_step_parts();
 const char *fast_part_name(int part);
 int fast_rows(int nx, int ny);

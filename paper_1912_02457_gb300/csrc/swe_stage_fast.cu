@@ -11,8 +11,12 @@
 //  * the CFL reduction is a warp/block max, and the last block of stage 2 to
 //    finish advances the device clock (t, dt, forcing brackets), so a step
 //    is two launches and needs no host round trip;
+//  * ghosts of nested edges read an edge-state buffer that stage 1 fills for
+//    the next time level; periodic ghosts read their periodic image;
+//  * one persistent kernel serves single domains (arguments in the launch's
+//    parameter space) and batches (a device tile table);
 //  * this translation unit is built with approximate FP32 reciprocal and
-//    square root (-prec-div=false -prec-sqrt=false): ~1 ulp, far inside the
+//    square root (-prec-div=false -prec-sqrt=false): ~2 ulp, far inside the
 //    parity tolerance, and exact zeros stay exact (lake at rest is still
 //    bit-exact).
 #include <cstring>
@@ -235,8 +239,8 @@ __device__ __forceinline__ Face<float> shfl_dn_face(const Face<float> &F) {
     return G;
 }
 
-// Advance the device clock after the last block of stage 2 (see
-// clock_update in swe_kernels.cu).
+// Advance the device clock after the last block of stage 2 (clock_update in
+// swe_device.cuh).
 __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks) {
     __shared__ unsigned int last;
     if (threadIdx.x == 0) {
