@@ -182,6 +182,7 @@ StageArgs<T> make_args(const swe_domain *d) {
     a.clk.dt_every = d->p.dt_update_every < 1 ? 1 : d->p.dt_update_every;
     a.clk.wind_uniform = (d->wind_n1 == 1 && d->wind_n2 == 1) ? 1 : 0;
     a.clk.rho_ratio = d->p.rho_air / d->p.rho_water;
+    a.clk.fp32 = d->prec == SWE_F64 ? 0 : 1;
     return a;
 }
 

@@ -316,8 +316,18 @@ __device__ inline void flag_error(StepCtl *ctl, int cell) {
     }
 }
 
-// The clock: t, dt and forcing brackets in FP64 (one thread per domain).
-__device__ __forceinline__ void bracket(const double *times, int n, double t, int *k, double *s) {
+// The clock (one thread per domain): t and dt in FP64; frame brackets with
+// their weights in the precision of the domain.
+// The FP32 clock arithmetic uses explicitly rounded operations: the clock
+// runs in translation units built with different division, square-root and
+// contraction settings, and must give the same bits in all of them (a
+// resumed run replays the clock of an uninterrupted one).
+__device__ __forceinline__ double frame_weight(double off, double len, bool fp32) {
+    return fp32 ? (double)__fdiv_rn((float)off, (float)len) : off / len;
+}
+
+__device__ __forceinline__ void bracket(const double *times, int n, double t, int *k, double *s,
+                                        bool fp32) {
     if (n <= 1) { *k = 0; *s = 0.0; return; }
     if (t <= times[0]) { *k = 0; *s = 0.0; return; }
     if (t >= times[n - 1]) { *k = n - 2; *s = 1.0; return; }
@@ -327,24 +337,26 @@ __device__ __forceinline__ void bracket(const double *times, int n, double t, in
         if (times[mid] <= t) lo = mid; else hi = mid;
     }
     *k = lo;
-    *s = (t - times[lo]) / (times[lo + 1] - times[lo]);
+    *s = frame_weight(t - times[lo], times[lo + 1] - times[lo], fp32);
 }
 
 // bracket(), trying the interval `hint` first: the forcing time only moves
 // forward, so the interval of the previous evaluation nearly always holds
 // (the frame times are strictly increasing, so the interval is unique and
-// both routes give the same k and s).
+// both routes give the same k and s). With fp32 the weight is the FP32
+// quotient of the FP64 offset and interval (all an FP32 domain uses; the
+// FP64 division is slow on GB300), and s holds it widened.
 __device__ __forceinline__ void bracket_hint(const double *times, int n, double t, int hint, int *k,
-                                             double *s) {
+                                             double *s, bool fp32) {
     if (n > 1 && hint >= 0 && hint < n - 1) {
         const double t0 = times[hint], t1 = times[hint + 1];
         if (t0 <= t && t < t1) {
             *k = hint;
-            *s = (t - t0) / (t1 - t0);
+            *s = frame_weight(t - t0, t1 - t0, fp32);
             return;
         }
     }
-    bracket(times, n, t, k, s);
+    bracket(times, n, t, k, s, fp32);
 }
 
 // Advance (mode 1) or set up (mode 0: dt from `speed`; mode 2: brackets
@@ -374,22 +386,36 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
     }
     int bk[2], wk[2];
     double bs[2], ws[2], tau[2][2];
+    const bool fp32 = clk.fp32 != 0;
     for (int q = 0; q < 2; q++) {
         const double tt = t + (q ? dt : 0.0);
-        bracket_hint(bnd.times, bnd.n, tt, bhint, &bk[q], &bs[q]);
-        bracket_hint(wind.times, wind.n, tt, whint, &wk[q], &ws[q]);
+        bracket_hint(bnd.times, bnd.n, tt, bhint, &bk[q], &bs[q], fp32);
+        bracket_hint(wind.times, wind.n, tt, whint, &wk[q], &ws[q], fp32);
         tau[q][0] = tau[q][1] = 0.0;
         if (wind.n > 0 && clk.wind_uniform) {
             const float *A = wind.frames + 2LL * wk[q];
             const float *B = wind.n > 1 ? A + 2 : A;
-            double w = ws[q];
-            double wx = (1.0 - w) * A[0] + w * B[0];
-            double wy = (1.0 - w) * A[1] + w * B[1];
-            double sp = sqrt(wx * wx + wy * wy);
-            double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
-            double k = clk.rho_ratio * cdrag * sp;
-            tau[q][0] = k * wx;
-            tau[q][1] = k * wy;
+            if (fp32) {
+                // Large & Pond stress (Section 3.5) in the precision the FP32
+                // stage kernels use it in
+                const float w = (float)ws[q], w1 = __fsub_rn(1.f, w);
+                const float wx = __fadd_rn(__fmul_rn(w1, A[0]), __fmul_rn(w, B[0]));
+                const float wy = __fadd_rn(__fmul_rn(w1, A[1]), __fmul_rn(w, B[1]));
+                const float sp = __fsqrt_rn(__fadd_rn(__fmul_rn(wx, wx), __fmul_rn(wy, wy)));
+                const float cdrag = sp < 11.f ? 1.2e-3f : __fmul_rn(__fadd_rn(0.49f, __fmul_rn(0.065f, sp)), 1e-3f);
+                const float k = __fmul_rn(__fmul_rn((float)clk.rho_ratio, cdrag), sp);
+                tau[q][0] = __fmul_rn(k, wx);
+                tau[q][1] = __fmul_rn(k, wy);
+            } else {
+                double w = ws[q];
+                double wx = (1.0 - w) * A[0] + w * B[0];
+                double wy = (1.0 - w) * A[1] + w * B[1];
+                double sp = sqrt(wx * wx + wy * wy);
+                double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
+                double k = clk.rho_ratio * cdrag * sp;
+                tau[q][0] = k * wx;
+                tau[q][1] = k * wy;
+            }
         }
     }
     ctl->last_speed = speed;
