@@ -15,6 +15,8 @@ INVALID = -1
 
 @pytest.fixture(scope="module")
 def L():
+    from paper_1912_02457_gb300 import build
+    build.build()
     return swe.load()
 
 

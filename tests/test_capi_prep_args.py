@@ -13,6 +13,8 @@ FAKE = C.c_void_p(0x10000)          # never dereferenced: the checks reject firs
 
 @pytest.fixture(scope="module")
 def L():
+    from paper_1912_02457_gb300 import build
+    build.build()
     return swe.load()
 
 
