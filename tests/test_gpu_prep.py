@@ -13,6 +13,12 @@ from paper_1912_02457_gb300 import swe, synth
 torch = pytest.importorskip("torch")
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1912_02457_gb300 import build
+    build.build()
+
+
 def _rough(nx, ny, seed):
     """Cell-average depths of the coastal recipe's kind: a spectral field
     with an eastward ramp, 5 - 3000 m."""
