@@ -88,6 +88,13 @@ struct swe_domain {
     // the FP32 fast path: the domain's tiling and arguments, handed to the
     // persistent stage kernel (the one batches use) with every launch
     swe::OneDomain one{};
+    // per row and 28-column strip: does it hold a wet cell (the land mask
+    // is fixed at creation), and the device lists of live warp items per
+    // tile height, kept until the domain is destroyed (captured graphs and
+    // batch tables point at them)
+    std::vector<unsigned char> wet;
+    struct ItemList { int rows, n; int *dev; };
+    std::vector<ItemList> item_lists;
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
     int parts() const { return fast() ? swe::fast_step_parts() : swe::ref_step_parts(); }
@@ -186,14 +193,71 @@ StageArgs<T> make_args(const swe_domain *d) {
     return a;
 }
 
+// The wet flags of the fast path's strips (once per domain).
+int ensure_wet(swe_domain *d) {
+    if (!d->wet.empty()) return SWE_OK;
+    const size_t n = (size_t)d->ny * swe::fast_strips(d->nx);
+    try {
+        d->wet.resize(n);
+    } catch (...) {
+        return SWE_ERR_OOM;
+    }
+    unsigned char *dev = (unsigned char *)d->dalloc(n);
+    if (!dev) { d->wet.clear(); return SWE_ERR_OOM; }
+    cudaError_t e = swe::launch_wet_strips((const float *)d->H, d->cpitch, d->nx, d->ny, dev, d->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d->wet.data(), dev, n, cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    d->dfree(dev);
+    if (e != cudaSuccess) { d->wet.clear(); return cuda_fail(e); }
+    return SWE_OK;
+}
+
+// The device list of live warp items for tile height `rows` (built once).
+int domain_items(swe_domain *d, int rows, const int **dev, int *n) {
+    for (const auto &l : d->item_lists)
+        if (l.rows == rows) { *dev = l.dev; *n = l.n; return SWE_OK; }
+    int rc = ensure_wet(d);
+    if (rc) return rc;
+    std::vector<int> items;
+    try {
+        swe::fast_items(d->nx, d->ny, rows, d->wet.data(), items);
+    } catch (...) {
+        return SWE_ERR_OOM;
+    }
+    int *p = (int *)d->dalloc(items.size() * sizeof(int));
+    if (!p) return SWE_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) { d->dfree(p); return cuda_fail(e); }
+    d->item_lists.push_back({rows, (int)items.size(), p});
+    *dev = p;
+    *n = (int)items.size();
+    return SWE_OK;
+}
+
+// Arguments of the fast path for tile height `rows`, its live items and
+// the blocks a launch over them takes.
+int fast_args(swe_domain *d, int rows, StageArgs<float> *a, int *tiles) {
+    const int *items = nullptr;
+    int n = 0;
+    int rc = domain_items(d, rows, &items, &n);
+    if (rc) return rc;
+    *a = make_args<float>(d);
+    a->items = items;
+    a->n_items = n;
+    *tiles = swe::fast_tiles(n);
+    return SWE_OK;
+}
+
 // (Re)compute the fast path's tiling and launch arguments (after creation
 // and whenever the forcing buffers change).
 int upload_table(swe_domain *d) {
     if (!d->fast()) return SWE_OK;
-    d->one.args = make_args<float>(d);
-    d->one.rows = swe::fast_rows(d->nx, d->ny);
-    d->one.tiles = swe::fast_tiles(d->nx, d->ny, d->one.rows, &d->one.strips);
-    return SWE_OK;
+    int rc = ensure_wet(d);
+    if (rc) return rc;
+    d->one.rows = swe::fast_rows(d->nx, d->ny, d->wet.data());
+    d->one.strips = swe::fast_strips(d->nx);
+    return fast_args(d, d->one.rows, &d->one.args, &d->one.tiles);
 }
 
 int upload_plane(swe_domain *d, void *dst, const void *src, int rows, int cols,
@@ -674,9 +738,12 @@ int batch_upload(swe_batch *b) {
     std::vector<swe::StageArgs<float>> args(n);
     std::vector<int> start(n + 1, 0), gx(n), rows(n);
     for (int k = 0; k < n; k++) {
-        args[k] = make_args<float>(b->doms[k]);
         rows[k] = b->rows[k];
-        start[k + 1] = start[k] + swe::fast_tiles(b->doms[k]->nx, b->doms[k]->ny, rows[k], &gx[k]);
+        int tiles = 0;
+        int rc = fast_args(b->doms[k], rows[k], &args[k], &tiles);
+        if (rc) return rc;
+        gx[k] = swe::fast_strips(b->doms[k]->nx);
+        start[k + 1] = start[k] + tiles;
     }
     // synchronous copies: the graph reads these tables; nothing is in flight
     CK(cudaStreamSynchronize(b->stream));
@@ -726,7 +793,7 @@ int batch_ensure_graph(swe_batch *b) {
 
 int batch_set_rows_all(swe_batch *b, int rows) {
     for (size_t k = 0; k < b->doms.size(); k++)
-        b->rows[k] = rows > 0 ? rows : swe::fast_rows(b->doms[k]->nx, b->doms[k]->ny);
+        b->rows[k] = rows > 0 ? rows : b->doms[k]->one.rows;
     return batch_upload(b);
 }
 
@@ -801,7 +868,7 @@ int swe_batch_add(swe_batch_handle b, swe_handle d) {
     if (step_check(d, 0)) return step_check(d, 0);
     CK(cudaStreamSynchronize(d->stream));      // creation and uploads finished
     b->doms.push_back(d);
-    b->rows.push_back(b->rows_choice > 0 ? b->rows_choice : swe::fast_rows(d->nx, d->ny));
+    b->rows.push_back(b->rows_choice > 0 ? b->rows_choice : d->one.rows);
     return batch_upload(b);
 }
 

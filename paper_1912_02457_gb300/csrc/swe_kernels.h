@@ -1,5 +1,7 @@
 // swe_kernels.h -- launchers of the libswe kernels (internal).
 #pragma once
+#include <vector>
+
 #include "swe_internal.h"
 
 namespace swe {
@@ -28,8 +30,16 @@ cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long
 // parameter space.
 int fast_step_parts();
 const char *fast_part_name(int part);
-int fast_rows(int nx, int ny);
-int fast_tiles(int nx, int ny, int rows, int *grid_x);
+// Tiling: each warp item is a strip of 28 output columns by `rows` rows,
+// numbered band * strips + strip; a launch covers the live items only
+// (those with a wet output cell). wet: ny x strips flags of
+// launch_wet_strips on the host, or NULL (every item live).
+int fast_strips(int nx);
+int fast_rows(int nx, int ny, const unsigned char *wet);
+void fast_items(int nx, int ny, int rows, const unsigned char *wet, std::vector<int> &items);
+int fast_tiles(int n_items);
+cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
+                              cudaStream_t st);
 int batch_grid_blocks();
 cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st);
 // The same kernel for one domain whose arguments travel with the launch.

@@ -19,7 +19,9 @@
 //    square root (-prec-div=false -prec-sqrt=false): ~2 ulp, far inside the
 //    parity tolerance, and exact zeros stay exact (lake at rest is still
 //    bit-exact).
+#include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "swe_device.cuh"
 #include "swe_kernels.h"
@@ -454,8 +456,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     const int warp = threadIdx.x >> 5;
     if (a.ctl->done) return;                       // forecast horizon reached (block-uniform)
     const int bands = (a.ny + rows - 1) / rows;
-    const int item = blk * kWarps + warp;
-    const bool strip_live = item < strips * bands;
+    // warp slot -> warp item (through the list of live items, if any)
+    const int slot = blk * kWarps + warp;
+    const bool strip_live = slot < (a.items ? a.n_items : strips * bands);
+    int item = slot;
+    if (a.items && strip_live) item = SWE_CHECK(a, slot, a.n_items) ? __ldg(a.items + slot) : 0;
     const int strip = strip_live ? item % strips : 0;
     const int band = strip_live ? item / strips : 0;
     StripCtx k;
@@ -584,18 +589,42 @@ static int warp_slots() {
     return slots;
 }
 
-int fast_rows(int nx, int ny) {
+int fast_strips(int nx) { return (nx + kStrip - 1) / kStrip; }
+
+// Live warp items of the tiling with `rows`-row bands for each tile height
+// 8..128, from per-strip prefix counts of the wet flags (`wet`: ny x strips,
+// row-major, from wet_strips_kernel; NULL: every item is live). Small
+// domains only (the counts take strips x (ny+1) ints); larger ones count
+// every item, which changes only the height chosen.
+int fast_rows(int nx, int ny, const unsigned char *wet) {
     // Score each tile height: the fraction of the last wave that is filled
     // (warp items / whole waves of resident warps) times the share of
     // useful rows (a halo row costs about a third of an output row: its
     // loads, primitives and a y-reconstruction).
     if (SWE_FORCE_ROWS > 0) return SWE_FORCE_ROWS;
-    const long long strips = (nx + kStrip - 1) / kStrip;
+    const int strips = fast_strips(nx);
+    std::vector<int> pre;
+    if (wet && (long long)strips * (ny + 1) <= (1LL << 24)) {
+        pre.assign((size_t)strips * (ny + 1), 0);
+        for (int s = 0; s < strips; s++) {
+            int *p = &pre[(size_t)s * (ny + 1)];
+            for (int j = 0; j < ny; j++) p[j + 1] = p[j] + wet[(size_t)j * strips + s];
+        }
+    }
     const double slots = warp_slots();
     int best = 8;
     double best_score = -1.0;
     for (int rows = 8; rows <= 128; rows++) {
-        long long items = strips * ((ny + rows - 1) / rows);
+        const int bands = (ny + rows - 1) / rows;
+        long long items = (long long)strips * bands;
+        if (!pre.empty()) {
+            items = 0;
+            for (int s = 0; s < strips; s++) {
+                const int *p = &pre[(size_t)s * (ny + 1)];
+                for (int b = 0; b < bands; b++) items += p[std::min((b + 1) * rows, ny)] > p[b * rows];
+            }
+            if (items < 1) items = 1;
+        }
         double waves = (double)items / slots;
         double fill = waves / (waves <= 1.0 ? 1.0 : (double)(long long)(waves + 0.999999));
         double useful = (double)rows / (rows + 4.0 / 3.0);
@@ -605,6 +634,19 @@ int fast_rows(int nx, int ny) {
     return best;
 }
 
+void fast_items(int nx, int ny, int rows, const unsigned char *wet, std::vector<int> &items) {
+    const int strips = fast_strips(nx), bands = (ny + rows - 1) / rows;
+    items.clear();
+    for (int b = 0; b < bands; b++)
+        for (int s = 0; s < strips; s++) {
+            bool live = wet == nullptr;
+            for (int j = b * rows; j < std::min((b + 1) * rows, ny) && !live; j++)
+                live = wet[(size_t)j * strips + s] != 0;
+            if (live) items.push_back(b * strips + s);
+        }
+    if (items.empty()) items.push_back(0);      // an all-land domain still runs its clock
+}
+
 int fast_step_parts() { return 2; }
 
 const char *fast_part_name(int part) {
@@ -612,12 +654,31 @@ const char *fast_part_name(int part) {
     return part >= 0 && part < 2 ? names[part] : "";
 }
 
-// Blocks (of kWarps warp items) a domain needs; *strips_out: strips per row.
-int fast_tiles(int nx, int ny, int rows, int *strips_out) {
-    int strips = (nx + kStrip - 1) / kStrip;
-    long long items = (long long)strips * ((ny + rows - 1) / rows);
-    if (strips_out) *strips_out = strips;
-    return (int)((items + kWarps - 1) / kWarps);
+// Blocks (of kWarps warp items) a launch over n_items items needs.
+int fast_tiles(int n_items) { return (n_items + kWarps - 1) / kWarps; }
+
+// Per row j and 28-column strip s (out[j * strips + s]): does the strip
+// hold a wet cell of row j (a cell is land when any of its corners is
+// LAND, as in decode_cell)?
+__global__ void wet_strips_kernel(const float *__restrict__ H, long long cpitch, int nx, int ny, int strips,
+                                  unsigned char *__restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)ny * strips) return;
+    const int j = (int)(t / strips), s = (int)(t % strips);
+    const int c0 = s * kStrip, c1 = min(c0 + kStrip, nx);
+    const float *r0 = H + (long long)j * cpitch, *r1 = r0 + cpitch;
+    bool wet = false;
+    for (int i = c0; i < c1 && !wet; i++)
+        wet = !(r0[i] == kLand || r0[i + 1] == kLand || r1[i] == kLand || r1[i + 1] == kLand);
+    out[t] = wet ? 1 : 0;
+}
+
+cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
+                              cudaStream_t st) {
+    const int strips = fast_strips(nx);
+    const long long n = (long long)ny * strips;
+    wet_strips_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(H, cpitch, nx, ny, strips, out);
+    return cudaGetLastError();
 }
 
 int batch_grid_blocks() {
