@@ -340,44 +340,89 @@ __device__ __forceinline__ void bracket(const double *times, int n, double t, in
     *s = frame_weight(t - times[lo], times[lo + 1] - times[lo], fp32);
 }
 
-// bracket(), trying the interval `hint` first: the forcing time only moves
-// forward, so the interval of the previous evaluation nearly always holds
-// (the frame times are strictly increasing, so the interval is unique and
-// both routes give the same k and s). With fp32 the weight is the FP32
-// quotient of the FP64 offset and interval (all an FP32 domain uses; the
-// FP64 division is slow on GB300), and s holds it widened.
-__device__ __forceinline__ void bracket_hint(const double *times, int n, double t, int hint, int *k,
-                                             double *s, bool fp32) {
-    if (n > 1 && hint >= 0 && hint < n - 1) {
-        const double t0 = times[hint], t1 = times[hint + 1];
-        if (t0 <= t && t < t1) {
-            *k = hint;
-            *s = frame_weight(t - t0, t1 - t0, fp32);
-            return;
-        }
+// The clock's inputs: its state of the previous step and the forcing values
+// around the previous brackets. They do not change while a stage kernel
+// runs (only the clock writes them, and it runs after every other block of
+// the domain has finished), so a stage-2 block can load them before it
+// knows whether it is the last one: the loads overlap its atomics.
+struct ClockIn {
+    double t, dt, t_end;
+    long long step;
+    int parity, done;
+    int bhint, whint;          // bracket of the previous stage-2 time
+    double bt0, bt1;           // boundary times[bhint], times[bhint + 1] (if a bracket)
+    double wt0, wt1;           // wind times around whint (if a bracket)
+    int wk_pre;                // wind frame whose uniform values follow (-1: none)
+    float wa[2], wb[2];        // uniform wind frames wk_pre and the next one
+};
+
+__device__ __forceinline__ bool hint_ok(const ForcingDev &F, int hint) {
+    return F.n > 1 && hint >= 0 && hint < F.n - 1;
+}
+
+// First level: the clock state (one round of independent loads).
+__device__ __forceinline__ void clock_load_state(const StepCtl *ctl, ClockIn &c) {
+    c.t = ctl->t;
+    c.dt = ctl->dt;
+    c.t_end = ctl->t_end;
+    c.step = ctl->step;
+    c.parity = ctl->parity;
+    c.done = ctl->done;
+    c.bhint = ctl->bk[1];
+    c.whint = ctl->wk[1];
+}
+
+// Second level: the frame times around the previous brackets and the
+// uniform wind frames there.
+__device__ __forceinline__ void clock_load_forcing(const ClockParams &clk, const ForcingDev &bnd,
+                                                   const ForcingDev &wind, ClockIn &c) {
+    c.bt0 = c.bt1 = c.wt0 = c.wt1 = 0.0;
+    if (hint_ok(bnd, c.bhint)) { c.bt0 = bnd.times[c.bhint]; c.bt1 = bnd.times[c.bhint + 1]; }
+    const bool wh = hint_ok(wind, c.whint);
+    if (wh) { c.wt0 = wind.times[c.whint]; c.wt1 = wind.times[c.whint + 1]; }
+    c.wk_pre = -1;
+    c.wa[0] = c.wa[1] = c.wb[0] = c.wb[1] = 0.f;
+    if (wind.n > 0 && clk.wind_uniform && (wh || wind.n == 1)) {
+        c.wk_pre = wh ? c.whint : 0;
+        const float *A = wind.frames + 2LL * c.wk_pre;
+        const float *B = wind.n > 1 ? A + 2 : A;
+        c.wa[0] = A[0]; c.wa[1] = A[1]; c.wb[0] = B[0]; c.wb[1] = B[1];
+    }
+}
+
+// bracket(), trying the interval `hint` (bounded by the preloaded t0, t1)
+// first: the forcing time only moves forward, so the interval of the
+// previous evaluation nearly always holds (the frame times are strictly
+// increasing, so the interval is unique and both routes give the same k
+// and s). With fp32 the weight is the FP32 quotient of the FP64 offset and
+// interval (all an FP32 domain uses; the FP64 division is slow on GB300),
+// and s holds it widened.
+__device__ __forceinline__ void bracket_pre(const double *times, int n, double t, int hint, double t0,
+                                            double t1, int *k, double *s, bool fp32) {
+    if (n > 1 && hint >= 0 && hint < n - 1 && t0 <= t && t < t1) {
+        *k = hint;
+        *s = frame_weight(t - t0, t1 - t0, fp32);
+        return;
     }
     bracket(times, n, t, k, s, fp32);
 }
 
 // Advance (mode 1) or set up (mode 0: dt from `speed`; mode 2: brackets
-// only) the clock. It runs on one thread at the end of every step, so the
-// state is read once into registers and written once at the end, and the
-// loads that do not depend on each other are issued together.
-__device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
-                             const ForcingDev &wind, double speed, int mode) {
-    double t = ctl->t, dt = ctl->dt;
-    long long step = ctl->step;
-    int parity = ctl->parity, done = ctl->done;
-    const int err0 = ctl->err;
-    const double t_end = ctl->t_end;
-    const int bhint = ctl->bk[1], whint = ctl->wk[1];
-    int err = err0;
+// only) the clock from its loaded inputs. It runs on one thread; the state
+// is written once at the end.
+__device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
+                                     const ForcingDev &wind, double speed, int mode, const ClockIn &c) {
+    double t = c.t, dt = c.dt;
+    long long step = c.step;
+    int parity = c.parity, done = c.done;
+    const double t_end = c.t_end;
+    bool bad_speed = false;
     if (mode == 1) { t += dt; step += 1; parity ^= 1; }
     if (clk.dt_fixed > 0.0) {
         dt = clk.dt_fixed;
     } else if (mode == 0 || (mode == 1 && step % clk.dt_every == 0)) {
         if (speed > 0.0 && isfinite(speed)) dt = clk.courant * 0.25 / speed;
-        else if (err == ERR_NONE) err = ERR_NUMERIC;
+        else bad_speed = true;
     }
     // a forecast horizon: clip the last step to land on t_end, then stop
     if (t_end > 0.0) {
@@ -389,18 +434,22 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
     const bool fp32 = clk.fp32 != 0;
     for (int q = 0; q < 2; q++) {
         const double tt = t + (q ? dt : 0.0);
-        bracket_hint(bnd.times, bnd.n, tt, bhint, &bk[q], &bs[q], fp32);
-        bracket_hint(wind.times, wind.n, tt, whint, &wk[q], &ws[q], fp32);
+        bracket_pre(bnd.times, bnd.n, tt, c.bhint, c.bt0, c.bt1, &bk[q], &bs[q], fp32);
+        bracket_pre(wind.times, wind.n, tt, c.whint, c.wt0, c.wt1, &wk[q], &ws[q], fp32);
         tau[q][0] = tau[q][1] = 0.0;
         if (wind.n > 0 && clk.wind_uniform) {
-            const float *A = wind.frames + 2LL * wk[q];
-            const float *B = wind.n > 1 ? A + 2 : A;
+            float a0 = c.wa[0], a1 = c.wa[1], b0 = c.wb[0], b1 = c.wb[1];
+            if (wk[q] != c.wk_pre) {
+                const float *A = wind.frames + 2LL * wk[q];
+                const float *B = wind.n > 1 ? A + 2 : A;
+                a0 = A[0]; a1 = A[1]; b0 = B[0]; b1 = B[1];
+            }
             if (fp32) {
                 // Large & Pond stress (Section 3.5) in the precision the FP32
                 // stage kernels use it in
                 const float w = (float)ws[q], w1 = __fsub_rn(1.f, w);
-                const float wx = __fadd_rn(__fmul_rn(w1, A[0]), __fmul_rn(w, B[0]));
-                const float wy = __fadd_rn(__fmul_rn(w1, A[1]), __fmul_rn(w, B[1]));
+                const float wx = __fadd_rn(__fmul_rn(w1, a0), __fmul_rn(w, b0));
+                const float wy = __fadd_rn(__fmul_rn(w1, a1), __fmul_rn(w, b1));
                 const float sp = __fsqrt_rn(__fadd_rn(__fmul_rn(wx, wx), __fmul_rn(wy, wy)));
                 const float cdrag = sp < 11.f ? 1.2e-3f : __fmul_rn(__fadd_rn(0.49f, __fmul_rn(0.065f, sp)), 1e-3f);
                 const float k = __fmul_rn(__fmul_rn((float)clk.rho_ratio, cdrag), sp);
@@ -408,8 +457,8 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
                 tau[q][1] = __fmul_rn(k, wy);
             } else {
                 double w = ws[q];
-                double wx = (1.0 - w) * A[0] + w * B[0];
-                double wy = (1.0 - w) * A[1] + w * B[1];
+                double wx = (1.0 - w) * a0 + w * b0;
+                double wy = (1.0 - w) * a1 + w * b1;
                 double sp = sqrt(wx * wx + wy * wy);
                 double cdrag = sp < 11.0 ? 1.2e-3 : (0.49 + 0.065 * sp) * 1e-3;
                 double k = clk.rho_ratio * cdrag * sp;
@@ -424,7 +473,9 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
     ctl->step = step;
     ctl->parity = parity;
     ctl->done = done;
-    if (err != err0) { ctl->err = err; ctl->err_step = step; }
+    // a non-finite or zero CFL maximum is an error unless one is recorded
+    // already (the sticky code is read here only, on this rare path)
+    if (bad_speed && ctl->err == ERR_NONE) { ctl->err = ERR_NUMERIC; ctl->err_step = step; }
     for (int q = 0; q < 2; q++) {
         ctl->bk[q] = bk[q]; ctl->bs[q] = bs[q];
         ctl->wk[q] = wk[q]; ctl->ws[q] = ws[q];
@@ -433,6 +484,14 @@ __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const 
         ctl->tau_f[q][0] = (float)tau[q][0];
         ctl->tau_f[q][1] = (float)tau[q][1];
     }
+}
+
+__device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
+                                    const ForcingDev &wind, double speed, int mode) {
+    ClockIn c;
+    clock_load_state(ctl, c);
+    clock_load_forcing(clk, bnd, wind, c);
+    clock_advance(ctl, clk, bnd, wind, speed, mode, c);
 }
 
 

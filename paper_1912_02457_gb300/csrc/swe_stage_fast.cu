@@ -244,21 +244,21 @@ __device__ __forceinline__ Face<float> shfl_dn_face(const Face<float> &F) {
 // Advance the device clock after the last block of stage 2 (clock_update in
 // swe_device.cuh).
 __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks) {
-    __shared__ unsigned int last;
-    if (threadIdx.x == 0) {
-        atomicMax(&a.ctl->speed32, __float_as_uint(block_speed));
-        __threadfence();
-        unsigned int prev = atomicAdd(&a.ctl->blocks_done, 1u);
-        last = (prev == (unsigned int)nblocks - 1u);
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        unsigned int bits = atomicExch(&a.ctl->speed32, 0u);
-        a.ctl->blocks_done = 0u;
-        clock_update(a.ctl, a.clk, a.bnd, a.wind, (double)__uint_as_float(bits), 1);
-        __threadfence();
-    }
+    if (threadIdx.x != 0) return;
+    atomicMax(&a.ctl->speed32, __float_as_uint(block_speed));
+    __threadfence();                           // the block's maximum lands before its count
+    // every block loads the clock's inputs while its count is in flight;
+    // the last one then needs no further round trip to memory
+    ClockIn c;
+    clock_load_state(a.ctl, c);
+    const unsigned int prev = atomicAdd(&a.ctl->blocks_done, 1u);
+    clock_load_forcing(a.clk, a.bnd, a.wind, c);
+    if (prev != (unsigned int)nblocks - 1u) return;
+    // atomics are performed at L2, so the exchange sees every block's
+    // maximum; the next kernel sees the clock's writes (kernel boundary)
+    const unsigned int bits = atomicExch(&a.ctl->speed32, 0u);
+    a.ctl->blocks_done = 0u;
+    clock_advance(a.ctl, a.clk, a.bnd, a.wind, (double)__uint_as_float(bits), 1, c);
 }
 
 }  // namespace
