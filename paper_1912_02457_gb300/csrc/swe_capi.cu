@@ -88,12 +88,13 @@ struct swe_domain {
     // the FP32 fast path: the domain's tiling and arguments, handed to the
     // persistent stage kernel (the one batches use) with every launch
     swe::OneDomain one{};
-    // per row and 28-column strip: does it hold a wet cell (the land mask
-    // is fixed at creation), and the device lists of live warp items per
-    // tile height, kept until the domain is destroyed (captured graphs and
-    // batch tables point at them)
+    // per 28-column strip and row: does it hold a wet cell (the land mask
+    // is fixed at creation); the work budget of the domain alone; the
+    // device plans (warp items) per budget, kept until the domain is
+    // destroyed (captured graphs and batch tables point at them)
     std::vector<unsigned char> wet;
-    struct ItemList { int rows, n; int *dev; };
+    int budget = 0;
+    struct ItemList { int budget, n; uint2 *dev; };
     std::vector<ItemList> item_lists;
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
@@ -196,7 +197,7 @@ StageArgs<T> make_args(const swe_domain *d) {
 // The wet flags of the fast path's strips (once per domain).
 int ensure_wet(swe_domain *d) {
     if (!d->wet.empty()) return SWE_OK;
-    const size_t n = (size_t)d->ny * swe::fast_strips(d->nx);
+    const size_t n = (size_t)swe::fast_strips(d->nx) * d->ny;
     try {
         d->wet.resize(n);
     } catch (...) {
@@ -212,35 +213,36 @@ int ensure_wet(swe_domain *d) {
     return SWE_OK;
 }
 
-// The device list of live warp items for tile height `rows` (built once).
-int domain_items(swe_domain *d, int rows, const int **dev, int *n) {
+// The device plan of the fast path for a work budget (built once).
+int domain_items(swe_domain *d, int budget, const uint2 **dev, int *n) {
     for (const auto &l : d->item_lists)
-        if (l.rows == rows) { *dev = l.dev; *n = l.n; return SWE_OK; }
+        if (l.budget == budget) { *dev = l.dev; *n = l.n; return SWE_OK; }
     int rc = ensure_wet(d);
     if (rc) return rc;
-    std::vector<int> items;
+    std::vector<uint2> items;
     try {
-        swe::fast_items(d->nx, d->ny, rows, d->wet.data(), items);
+        swe::fast_plan(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width, budget, items);
     } catch (...) {
         return SWE_ERR_OOM;
     }
-    int *p = (int *)d->dalloc(items.size() * sizeof(int));
+    uint2 *p = (uint2 *)d->dalloc(items.size() * sizeof(uint2));
     if (!p) return SWE_ERR_OOM;
-    cudaError_t e = cudaMemcpyAsync(p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, d->stream);
+    cudaError_t e = cudaMemcpyAsync(p, items.data(), items.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                                    d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) { d->dfree(p); return cuda_fail(e); }
-    d->item_lists.push_back({rows, (int)items.size(), p});
+    d->item_lists.push_back({budget, (int)items.size(), p});
     *dev = p;
     *n = (int)items.size();
     return SWE_OK;
 }
 
-// Arguments of the fast path for tile height `rows`, its live items and
-// the blocks a launch over them takes.
-int fast_args(swe_domain *d, int rows, StageArgs<float> *a, int *tiles) {
-    const int *items = nullptr;
+// Arguments of the fast path for a work budget, its plan and the blocks a
+// launch over it takes.
+int fast_args(swe_domain *d, int budget, StageArgs<float> *a, int *tiles) {
+    const uint2 *items = nullptr;
     int n = 0;
-    int rc = domain_items(d, rows, &items, &n);
+    int rc = domain_items(d, budget, &items, &n);
     if (rc) return rc;
     *a = make_args<float>(d);
     a->items = items;
@@ -255,9 +257,10 @@ int upload_table(swe_domain *d) {
     if (!d->fast()) return SWE_OK;
     int rc = ensure_wet(d);
     if (rc) return rc;
-    d->one.rows = swe::fast_rows(d->nx, d->ny, d->wet.data());
+    if (!d->budget) d->budget = swe::fast_budget(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width);
+    d->one.rows = d->budget / swe::kPlanUnit;
     d->one.strips = swe::fast_strips(d->nx);
-    return fast_args(d, d->one.rows, &d->one.args, &d->one.tiles);
+    return fast_args(d, d->budget, &d->one.args, &d->one.tiles);
 }
 
 int upload_plane(swe_domain *d, void *dst, const void *src, int rows, int cols,
@@ -714,7 +717,7 @@ struct swe_batch {
     cudaStream_t capture_stream = nullptr;
     int cap = 0;
     std::vector<swe_handle> doms;
-    std::vector<int> rows;          // tile height per domain
+    std::vector<int> budget;        // work budget per domain (swe::kPlanUnit per row)
     int rows_choice = 0;            // 0: autotune on the next long step
     bool tuned = false;
     // device tables (capacity `cap`)
@@ -738,9 +741,9 @@ int batch_upload(swe_batch *b) {
     std::vector<swe::StageArgs<float>> args(n);
     std::vector<int> start(n + 1, 0), gx(n), rows(n);
     for (int k = 0; k < n; k++) {
-        rows[k] = b->rows[k];
+        rows[k] = b->budget[k] / swe::kPlanUnit;
         int tiles = 0;
-        int rc = fast_args(b->doms[k], rows[k], &args[k], &tiles);
+        int rc = fast_args(b->doms[k], b->budget[k], &args[k], &tiles);
         if (rc) return rc;
         gx[k] = swe::fast_strips(b->doms[k]->nx);
         start[k + 1] = start[k] + tiles;
@@ -793,7 +796,7 @@ int batch_ensure_graph(swe_batch *b) {
 
 int batch_set_rows_all(swe_batch *b, int rows) {
     for (size_t k = 0; k < b->doms.size(); k++)
-        b->rows[k] = rows > 0 ? rows : b->doms[k]->one.rows;
+        b->budget[k] = rows > 0 ? rows * swe::kPlanUnit : b->doms[k]->budget;
     return batch_upload(b);
 }
 
@@ -868,7 +871,7 @@ int swe_batch_add(swe_batch_handle b, swe_handle d) {
     if (step_check(d, 0)) return step_check(d, 0);
     CK(cudaStreamSynchronize(d->stream));      // creation and uploads finished
     b->doms.push_back(d);
-    b->rows.push_back(b->rows_choice > 0 ? b->rows_choice : d->one.rows);
+    b->budget.push_back(b->rows_choice > 0 ? b->rows_choice * swe::kPlanUnit : d->budget);
     return batch_upload(b);
 }
 
@@ -877,7 +880,7 @@ int swe_batch_remove(swe_batch_handle b, swe_handle d) {
     for (size_t k = 0; k < b->doms.size(); k++)
         if (b->doms[k] == d) {
             b->doms.erase(b->doms.begin() + (long)k);
-            b->rows.erase(b->rows.begin() + (long)k);
+            b->budget.erase(b->budget.begin() + (long)k);
             return batch_upload(b);             // also drains the batch stream
         }
     return SWE_ERR_INVALID_ARG;

@@ -420,7 +420,7 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
     if (mode == 1) { t += dt; step += 1; parity ^= 1; }
     if (clk.dt_fixed > 0.0) {
         dt = clk.dt_fixed;
-    } else if (mode == 0 || (mode == 1 && step % clk.dt_every == 0)) {
+    } else if (mode == 0 || (mode == 1 && (clk.dt_every == 1 || step % clk.dt_every == 0))) {
         if (speed > 0.0 && isfinite(speed)) dt = clk.courant * 0.25 / speed;
         else bad_speed = true;
     }

@@ -82,11 +82,10 @@ struct StageArgs {
     // 12 nx + 6 ny; within an edge of length n, value v of ring r at
     // position k sits at (3 r + v) n + k.
     float *edge;
-    // FP32 fast path: the warp items a launch covers, each band * strips +
-    // strip of the tiling the launch uses, ascending: only the items with at
-    // least one wet output cell (an all-land item writes nothing). NULL:
-    // every item of the tiling.
-    const int *items;
+    // FP32 fast path: the warp items a launch covers, {strip, j0 | rows << 16}
+    // (rows without a wet cell in the strip are left out: land cells are
+    // never written). NULL: every strip of `rows`-row bands.
+    const uint2 *items;
     int n_items;
     // elements of each buffer (checked by the bounds-checked debug builds)
     long long n_plane, n_corner, n_edge, n_bnd, n_wind;

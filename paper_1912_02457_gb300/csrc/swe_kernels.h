@@ -30,13 +30,16 @@ cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long
 // parameter space.
 int fast_step_parts();
 const char *fast_part_name(int part);
-// Tiling: each warp item is a strip of 28 output columns by `rows` rows,
-// numbered band * strips + strip; a launch covers the live items only
-// (those with a wet output cell). wet: ny x strips flags of
-// launch_wet_strips on the host, or NULL (every item live).
+// Work planning (swe_stage_fast.cu): a warp item is a strip of 28 output
+// columns by a run of rows, packed as {strip, j0 | rows << 16}; a launch
+// covers the items of the domain's plan. Budgets cap the cost of an item in
+// kPlanUnit per plain row. wet: strips x ny flags of launch_wet_strips
+// (strip-major) on the host, or NULL (every cell wet).
+constexpr int kPlanUnit = 100;
 int fast_strips(int nx);
-int fast_rows(int nx, int ny, const unsigned char *wet);
-void fast_items(int nx, int ny, int rows, const unsigned char *wet, std::vector<int> &items);
+int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width);
+void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width, int budget,
+               std::vector<uint2> &items);
 int fast_tiles(int n_items);
 cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
                               cudaStream_t st);

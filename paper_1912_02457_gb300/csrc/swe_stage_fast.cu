@@ -20,6 +20,7 @@
 //    parity tolerance, and exact zeros stay exact (lake at rest is still
 //    bit-exact).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -455,19 +456,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (a.ctl->done) return;                       // forecast horizon reached (block-uniform)
-    const int bands = (a.ny + rows - 1) / rows;
-    // warp slot -> warp item (through the list of live items, if any)
+    // warp slot -> warp item: from the domain's plan, or (without one) the
+    // item-th strip of `rows`-row bands
     const int slot = blk * kWarps + warp;
-    const bool strip_live = slot < (a.items ? a.n_items : strips * bands);
-    int item = slot;
-    if (a.items && strip_live) item = SWE_CHECK(a, slot, a.n_items) ? __ldg(a.items + slot) : 0;
-    const int strip = strip_live ? item % strips : 0;
-    const int band = strip_live ? item / strips : 0;
+    bool strip_live;
+    int strip = 0, j0 = 0, j1 = 0;
+    if (a.items) {
+        strip_live = slot < a.n_items;
+        if (strip_live && SWE_CHECK(a, slot, a.n_items)) {
+            const uint2 it = __ldg(a.items + slot);
+            strip = (int)it.x;
+            j0 = (int)(it.y & 0xffffu);
+            j1 = min(j0 + (int)(it.y >> 16), a.ny);
+        }
+    } else {
+        const int bands = (a.ny + rows - 1) / rows;
+        strip_live = slot < strips * bands;
+        if (strip_live) { strip = slot % strips; j0 = slot / strips * rows; j1 = min(j0 + rows, a.ny); }
+    }
     StripCtx k;
     k.lane = lane;
     k.i = strip * kStrip - 2 + lane;
-    k.j0 = band * rows;
-    k.j1 = min(k.j0 + rows, a.ny);
+    k.j0 = j0;
+    k.j1 = j1;
     k.par = a.ctl->parity;
     // stage 1 also evaluates the external edge state of the next time level
     // (used by stage 2 and by stage 1 of the next step); the interior
@@ -589,62 +600,142 @@ static int warp_slots() {
     return slots;
 }
 
-int fast_strips(int nx) { return (nx + kStrip - 1) / kStrip; }
+// ---------------------------------------------------------------------------
+// work planning: warp items of variable height
+//
+// A warp item is a strip of 28 output columns by a run of rows
+// [j0, j0 + n), packed as {strip, j0 | n << 16}. A row costs about the same
+// everywhere except in the strips whose two outer lanes are ghosts of a
+// nested edge (they take the edge-state path: ~8% more per row) and, in
+// stage 2, in flow-relaxation zones (~10% more); the four halo rows a march
+// adds cost about a third of a row each. Rows without a wet cell in the
+// strip are left out (land cells are never written and never enter the CFL
+// maximum, and a march recomputes its own halo): each strip falls into
+// segments of wet rows, split where a land run is longer than a halo. A
+// budget (kPlanUnit per plain row) cuts a segment of cost C into
+// ceil(C / budget) items of equal cost, so the item count follows the
+// budget smoothly and fast_budget can fill the GPU's resident warp slots.
 
-// Live warp items of the tiling with `rows`-row bands for each tile height
-// 8..128, from per-strip prefix counts of the wet flags (`wet`: ny x strips,
-// row-major, from wet_strips_kernel; NULL: every item is live). Small
-// domains only (the counts take strips x (ny+1) ints); larger ones count
-// every item, which changes only the height chosen.
-int fast_rows(int nx, int ny, const unsigned char *wet) {
-    // Score each tile height: the fraction of the last wave that is filled
-    // (warp items / whole waves of resident warps) times the share of
-    // useful rows (a halo row costs about a third of an output row: its
-    // loads, primitives and a y-reconstruction).
-    if (SWE_FORCE_ROWS > 0) return SWE_FORCE_ROWS;
-    const int strips = fast_strips(nx);
-    std::vector<int> pre;
-    if (wet && (long long)strips * (ny + 1) <= (1LL << 24)) {
-        pre.assign((size_t)strips * (ny + 1), 0);
-        for (int s = 0; s < strips; s++) {
-            int *p = &pre[(size_t)s * (ny + 1)];
-            for (int j = 0; j < ny; j++) p[j + 1] = p[j] + wet[(size_t)j * strips + s];
+namespace {
+
+constexpr int kGhostCost = 8, kFrsCost = 10, kHaloCost = 133;
+
+struct PlanCtx {
+    int nx, ny, strips, fw;
+    bool nest[4];
+    const unsigned char *wet;       // strips x ny, strip-major; NULL: all wet
+    bool is_wet(int j, int s) const { return !wet || wet[(size_t)s * ny + j] != 0; }
+    int strip_extra(int s) const {
+        int c = 0;
+        if ((s == 0 && nest[EDGE_W]) || (s == strips - 1 && nest[EDGE_E])) c += kGhostCost;
+        const int c0 = s * kStrip, c1 = std::min(c0 + kStrip, nx);
+        if ((nest[EDGE_W] && c0 < fw) || (nest[EDGE_E] && c1 > nx - fw)) c += kFrsCost;
+        return c;
+    }
+    int row_cost(int j, int s, int xs) const {
+        const bool frs = is_wet(j, s) && ((nest[EDGE_S] && j < fw) || (nest[EDGE_N] && j >= ny - fw));
+        return kPlanUnit + xs + (frs ? kFrsCost : 0);
+    }
+};
+
+struct Segment {
+    int strip, start, rows;
+    long long cost;
+};
+
+PlanCtx plan_ctx(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width) {
+    PlanCtx p;
+    p.nx = nx; p.ny = ny; p.strips = (nx + kStrip - 1) / kStrip; p.fw = frs_width; p.wet = wet;
+    for (int e = 0; e < 4; e++) p.nest[e] = bc[e] == BC_NESTED;
+    return p;
+}
+
+std::vector<Segment> plan_segments(const PlanCtx &p) {
+    std::vector<Segment> seg;
+    for (int s = 0; s < p.strips; s++) {
+        const int xs = p.strip_extra(s);
+        int j = 0;
+        for (;;) {
+            while (j < p.ny && !p.is_wet(j, s)) j++;
+            if (j >= p.ny) break;
+            const int start = j;
+            int end = j;                // one past the last wet row
+            while (j < p.ny) {
+                if (p.is_wet(j, s)) { end = ++j; continue; }
+                int L = 0;
+                while (j + L < p.ny && !p.is_wet(j + L, s)) L++;
+                if (j + L >= p.ny || L * kPlanUnit >= kHaloCost) break;
+                j += L;
+            }
+            long long c = 0;
+            for (int r = start; r < end; r++) c += p.row_cost(r, s, xs);
+            seg.push_back({s, start, end - start, c});
+            j = end;
         }
     }
+    return seg;
+}
+
+// items of one segment under a budget
+long long seg_items(const Segment &g, int budget) {
+    return std::min<long long>(g.rows, std::max<long long>(1, (g.cost + budget - 1) / budget));
+}
+
+}  // namespace
+
+int fast_strips(int nx) { return (nx + kStrip - 1) / kStrip; }
+
+int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width) {
+    if (SWE_FORCE_ROWS > 0) return SWE_FORCE_ROWS * kPlanUnit;
+    const std::vector<Segment> seg = plan_segments(plan_ctx(nx, ny, wet, bc, frs_width));
+    // Score: the fraction of the last wave filled (items / whole waves of
+    // resident warps) times the share of the work that is not halo.
     const double slots = warp_slots();
-    int best = 8;
+    int best = 8 * kPlanUnit;
     double best_score = -1.0;
-    for (int rows = 8; rows <= 128; rows++) {
-        const int bands = (ny + rows - 1) / rows;
-        long long items = (long long)strips * bands;
-        if (!pre.empty()) {
-            items = 0;
-            for (int s = 0; s < strips; s++) {
-                const int *p = &pre[(size_t)s * (ny + 1)];
-                for (int b = 0; b < bands; b++) items += p[std::min((b + 1) * rows, ny)] > p[b * rows];
-            }
-            if (items < 1) items = 1;
+    for (int b = 8 * kPlanUnit; b <= 128 * kPlanUnit; b += kPlanUnit / 20) {
+        long long n = 0, work = 0;
+        for (const Segment &g : seg) {
+            const long long k = seg_items(g, b);
+            n += k;
+            work += g.cost + k * kHaloCost;
         }
-        double waves = (double)items / slots;
-        double fill = waves / (waves <= 1.0 ? 1.0 : (double)(long long)(waves + 0.999999));
-        double useful = (double)rows / (rows + 4.0 / 3.0);
-        double score = fill * useful;
-        if (score > best_score + 1e-9) { best_score = score; best = rows; }
+        if (n == 0) return 8 * kPlanUnit;      // all land: one no-op item whatever the budget
+        const double waves = (double)n / slots;
+        const double fill = waves / (waves <= 1.0 ? 1.0 : std::ceil(waves - 1e-9));
+        const double useful = (double)(work - n * kHaloCost) / (double)work;
+        const double score = fill * useful;
+        if (score > best_score + 1e-12) { best_score = score; best = b; }
     }
     return best;
 }
 
-void fast_items(int nx, int ny, int rows, const unsigned char *wet, std::vector<int> &items) {
-    const int strips = fast_strips(nx), bands = (ny + rows - 1) / rows;
+void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width, int budget,
+               std::vector<uint2> &items) {
     items.clear();
-    for (int b = 0; b < bands; b++)
-        for (int s = 0; s < strips; s++) {
-            bool live = wet == nullptr;
-            for (int j = b * rows; j < std::min((b + 1) * rows, ny) && !live; j++)
-                live = wet[(size_t)j * strips + s] != 0;
-            if (live) items.push_back(b * strips + s);
+    const PlanCtx p = plan_ctx(nx, ny, wet, bc, frs_width);
+    std::vector<long long> pref;
+    for (const Segment &g : plan_segments(p)) {
+        const int xs = p.strip_extra(g.strip);
+        pref.assign((size_t)g.rows + 1, 0);
+        for (int r = 0; r < g.rows; r++) pref[r + 1] = pref[r] + p.row_cost(g.start + r, g.strip, xs);
+        const int k = (int)seg_items(g, budget);
+        // cut where the cost prefix is nearest to cost * q / k, each item
+        // keeping at least one row
+        int r0 = 0;
+        for (int q = 1; q <= k; q++) {
+            int r1 = g.rows;
+            if (q < k) {
+                const long long target = g.cost * q / k;
+                r1 = r0 + 1;
+                while (r1 < g.rows - (k - q) && pref[r1] < target) r1++;
+                if (r1 - 1 > r0 && target - pref[r1 - 1] < pref[r1] - target) r1--;
+            }
+            items.push_back(make_uint2((unsigned)g.strip, (unsigned)(g.start + r0) | ((unsigned)(r1 - r0) << 16)));
+            r0 = r1;
         }
-    if (items.empty()) items.push_back(0);      // an all-land domain still runs its clock
+    }
+    if (items.empty()) items.push_back(make_uint2(0u, 1u << 16));   // all land: a no-op item runs the clock
 }
 
 int fast_step_parts() { return 2; }
@@ -657,9 +748,9 @@ const char *fast_part_name(int part) {
 // Blocks (of kWarps warp items) a launch over n_items items needs.
 int fast_tiles(int n_items) { return (n_items + kWarps - 1) / kWarps; }
 
-// Per row j and 28-column strip s (out[j * strips + s]): does the strip
-// hold a wet cell of row j (a cell is land when any of its corners is
-// LAND, as in decode_cell)?
+// Per 28-column strip s and row j (out[s * ny + j], strip-major for the
+// planner's walk down each strip): does the strip hold a wet cell of row j
+// (a cell is land when any of its corners is LAND, as in decode_cell)?
 __global__ void wet_strips_kernel(const float *__restrict__ H, long long cpitch, int nx, int ny, int strips,
                                   unsigned char *__restrict__ out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -670,7 +761,7 @@ __global__ void wet_strips_kernel(const float *__restrict__ H, long long cpitch,
     bool wet = false;
     for (int i = c0; i < c1 && !wet; i++)
         wet = !(r0[i] == kLand || r0[i + 1] == kLand || r1[i] == kLand || r1[i + 1] == kLand);
-    out[t] = wet ? 1 : 0;
+    out[(long long)s * ny + j] = wet ? 1 : 0;
 }
 
 cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
