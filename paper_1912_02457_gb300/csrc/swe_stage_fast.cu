@@ -736,6 +736,12 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
         }
     }
     if (items.empty()) items.push_back(make_uint2(0u, 1u << 16));   // all land: a no-op item runs the clock
+    // row-major order: a block's warps take neighbouring strips of the same
+    // rows (they share halo lines in L1), and every SM gets a mix of strips
+    std::sort(items.begin(), items.end(), [](const uint2 &a, const uint2 &b) {
+        const unsigned ja = a.y & 0xffffu, jb = b.y & 0xffffu;
+        return ja != jb ? ja < jb : a.x < b.x;
+    });
 }
 
 int fast_step_parts() { return 2; }
