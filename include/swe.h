@@ -158,7 +158,8 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times,
  * asynchronously on the domain's stream. Each step: stage 1 at t, stage 2
  * at t + dt, flow relaxation, then the fused CFL reduction sets the next
  * dt on the device (no host synchronisation). Runs of 16 steps replay one
- * CUDA graph (captured on first use, rebuilt after swe_set_forcing).
+ * CUDA graph and the remaining steps a one-step graph (both captured on
+ * first use, rebuilt after swe_set_forcing).
  * Numerical failures are reported through swe_get_info / the next
  * synchronising call.
  * Errors: SWE_ERR_INVALID_ARG, SWE_ERR_CUDA (launch), SWE_ERR_NUMERIC

@@ -73,16 +73,18 @@ struct swe_domain {
     long long launches = 0;
     std::vector<cudaEvent_t> events;   // profiling pool, grown on demand
 
-    // graph of kGraphSteps steps, captured on a private stream and replayed
-    // on `stream`; every kernel reads the parity and clock from the device,
-    // so one graph serves every step until the forcing buffers change
+    // graphs of kGraphSteps steps and of one step, captured on a private
+    // stream and replayed on `stream`; every kernel reads the parity and
+    // clock from the device, so a graph serves every step until the forcing
+    // buffers change
     static constexpr int kGraphSteps = 16;
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr, graph1 = nullptr;
 
     void drop_graph() {
         if (graph) cudaGraphExecDestroy(graph);
-        graph = nullptr;
+        if (graph1) cudaGraphExecDestroy(graph1);
+        graph = graph1 = nullptr;
     }
 
     // the FP32 fast path: the domain's tiling and arguments, handed to the
@@ -527,20 +529,20 @@ int launch_part(swe_handle h, int part) {
     return rc;
 }
 
-int ensure_graph(swe_handle h) {
-    if (h->graph) return SWE_OK;
+int ensure_graph(swe_handle h, int steps, cudaGraphExec_t *out) {
+    if (*out) return SWE_OK;
     if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
     int rc = SWE_OK;
-    for (int s = 0; s < swe_domain::kGraphSteps && !rc; s++)
+    for (int s = 0; s < steps && !rc; s++)
         for (int p = 0; p < h->parts() && !rc; p++) rc = launch_part_on(h, p, h->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(e); }
+    if (e != cudaSuccess) { *out = nullptr; return cuda_fail(e); }
     return SWE_OK;
 }
 
@@ -553,15 +555,19 @@ int swe_step(swe_handle h, int n_steps) {
     const int parts = h->parts();
     const int G = swe_domain::kGraphSteps;
     if (n_steps >= G) {
-        if ((rc = ensure_graph(h))) return rc;
+        if ((rc = ensure_graph(h, G, &h->graph))) return rc;
         for (; n_steps >= G; n_steps -= G) {
             CK(cudaGraphLaunch(h->graph, h->stream));
             h->launches += (long long)G * parts;
         }
     }
-    for (int s = 0; s < n_steps; s++)
-        for (int p = 0; p < parts; p++)
-            if ((rc = launch_part(h, p))) return rc;
+    // the remaining steps replay the one-step graph (its launches follow
+    // each other without a host round trip between them)
+    if (n_steps > 0 && (rc = ensure_graph(h, 1, &h->graph1))) return rc;
+    for (; n_steps > 0; n_steps--) {
+        CK(cudaGraphLaunch(h->graph1, h->stream));
+        h->launches += parts;
+    }
     return SWE_OK;
 }
 

@@ -606,8 +606,9 @@ static int warp_slots() {
 // A warp item is a strip of 28 output columns by a run of rows
 // [j0, j0 + n), packed as {strip, j0 | n << 16}. A row costs about the same
 // everywhere except in the strips whose two outer lanes are ghosts of a
-// nested edge (they take the edge-state path: ~8% more per row) and, in
-// stage 2, in flow-relaxation zones (~10% more); the four halo rows a march
+// nested edge (they take the edge-state path: ~10% more per row) and, in
+// stage 2, in flow-relaxation zones (~13% more; both measured per item on
+// the coastal 1024 x 1024 step); the four halo rows a march
 // adds cost about a third of a row each. Rows without a wet cell in the
 // strip are left out (land cells are never written and never enter the CFL
 // maximum, and a march recomputes its own halo): each strip falls into
@@ -618,7 +619,7 @@ static int warp_slots() {
 
 namespace {
 
-constexpr int kGhostCost = 8, kFrsCost = 10, kHaloCost = 133;
+constexpr int kGhostCost = 10, kFrsCost = 13, kHaloCost = 133;
 
 struct PlanCtx {
     int nx, ny, strips, fw;
