@@ -729,6 +729,8 @@ struct swe_batch {
     // device tables (capacity `cap`)
     swe::StageArgs<float> *d_args = nullptr;
     int *d_tile_start = nullptr, *d_grid_x = nullptr, *d_rows = nullptr, *d_n = nullptr;
+    int *d_tile_dom = nullptr;      // domain of each tile (capacity tile_dom_cap)
+    int tile_dom_cap = 0;
     int *d_done = nullptr;
     double *d_t = nullptr;
     int blocks = 0;
@@ -763,6 +765,28 @@ int batch_upload(swe_batch *b) {
     }
     CK(cudaMemcpy(b->d_tile_start, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_n, &n, sizeof(int), cudaMemcpyHostToDevice));
+    // one block per tile: a new tile count (or table) needs a new graph
+    const int blocks = start[n] > 0 ? start[n] : 1;
+    bool regraph = blocks != b->blocks;
+    if (start[n] > b->tile_dom_cap) {
+        int *p = nullptr;
+        CK(cudaMalloc(&p, sizeof(int) * (size_t)start[n]));
+        cudaFree(b->d_tile_dom);
+        b->d_tile_dom = p;
+        b->tile_dom_cap = start[n];
+        regraph = true;
+    }
+    if (start[n] > 0) {
+        std::vector<int> dom((size_t)start[n]);
+        for (int k = 0; k < n; k++)
+            for (int t = start[k]; t < start[k + 1]; t++) dom[(size_t)t] = k;
+        CK(cudaMemcpy(b->d_tile_dom, dom.data(), sizeof(int) * dom.size(), cudaMemcpyHostToDevice));
+    }
+    if (regraph) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->blocks = blocks;
+    }
     return SWE_OK;
 }
 
@@ -770,6 +794,7 @@ swe::BatchTable batch_table(const swe_batch *b) {
     swe::BatchTable t;
     t.args = b->d_args;
     t.tile_start = b->d_tile_start;
+    t.tile_dom = b->d_tile_dom;
     t.grid_x = b->d_grid_x;
     t.rows = b->d_rows;
     t.n_domains = b->d_n;
@@ -857,10 +882,9 @@ int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out) {
               cudaMalloc(&b->d_done, sizeof(int) * max_domains) == cudaSuccess &&
               cudaMalloc(&b->d_t, sizeof(double) * max_domains) == cudaSuccess;
     if (ok) ok = batch_upload(b) == SWE_OK;
-    if (ok) b->blocks = swe::batch_grid_blocks();
     if (!ok) {
         cudaFree(b->d_args); cudaFree(b->d_tile_start); cudaFree(b->d_grid_x); cudaFree(b->d_rows);
-        cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t);
+        cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t); cudaFree(b->d_tile_dom);
         delete b;
         return SWE_ERR_OOM;
     }
@@ -968,7 +992,7 @@ int swe_batch_destroy(swe_batch_handle b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     cudaFree(b->d_args); cudaFree(b->d_tile_start); cudaFree(b->d_grid_x); cudaFree(b->d_rows);
-    cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t);
+    cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t); cudaFree(b->d_tile_dom);
     delete b;
     return e == cudaSuccess ? SWE_OK : cuda_fail(e);
 }

@@ -102,6 +102,7 @@ struct OneDomain {
 struct BatchTable {
     const StageArgs<float> *args;   // per domain
     const int *tile_start;          // n+1 prefix sums of tiles per domain
+    const int *tile_dom;            // domain of each tile
     const int *grid_x;              // 28-column strips per row of each domain
     const int *rows;                // tile height of each domain
     const int *n_domains;           // current number of domains (device)

@@ -43,7 +43,6 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
 int fast_tiles(int n_items);
 cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
                               cudaStream_t st);
-int batch_grid_blocks();
 cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st);
 // The same kernel for one domain whose arguments travel with the launch.
 cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st);
