@@ -691,11 +691,14 @@ int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int f
     // resident warps) times the share of the work that is not halo. Items
     // are kept to 32 rows or fewer: longer marches measured slower on every
     // domain that needs them (2048^2 to 8192^2 coastal: 6-12%), even where
-    // they would fill the slots exactly.
+    // they would fill the slots exactly. Small domains take items down to two
+    // rows: a warp's march is a chain of dependent row iterations, so short
+    // items on more warps finish sooner (350^2: 35%, 512^2: 20% faster than
+    // items of eight rows or more).
     const double slots = warp_slots();
-    int best = 8 * kPlanUnit;
+    int best = 2 * kPlanUnit;
     double best_score = -1.0;
-    for (int b = 8 * kPlanUnit; b <= 32 * kPlanUnit; b += kPlanUnit / 20) {
+    for (int b = 2 * kPlanUnit; b <= 32 * kPlanUnit; b += kPlanUnit / 20) {
         long long n = 0, work = 0;
         for (const Segment &g : seg) {
             const long long k = seg_items(g, b);
