@@ -231,13 +231,11 @@ size_t bathy_bytes(int nx, int ny) {
 // ---------------------------------------------------------------------------
 // land erosion (Section 3.8)
 
-__global__ void __launch_bounds__(kBX * kBY) erode_kernel(const unsigned char *land, const float *eta,
-                                                          const float *Hm, long long pitch, int nx,
-                                                          int ny, float land_depth, unsigned char *land_out,
-                                                          float *eta_out, float *Hm_out) {
-    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
-    if (i >= nx || j >= ny) return;
+// One cell (i, j) of the erosion step (shared by the one-cell kernel and the
+// ragged end of a row in the four-cell kernel).
+__device__ __forceinline__ void erode_cell(const unsigned char *land, const float *eta, const float *Hm,
+                                           long long pitch, int nx, int ny, float land_depth, int i, int j,
+                                           unsigned char *land_out, float *eta_out, float *Hm_out) {
     const long long s = (long long)j * pitch + i;
     const bool l = land[s] != 0;
     // outside the domain counts as land
@@ -259,6 +257,68 @@ __global__ void __launch_bounds__(kBX * kBY) erode_kernel(const unsigned char *l
     land_out[s] = stays ? 1 : 0;
     eta_out[s] = e;
     Hm_out[s] = h;
+}
+
+__global__ void __launch_bounds__(kBX * kBY) erode_kernel(const unsigned char *land, const float *eta,
+                                                          const float *Hm, long long pitch, int nx,
+                                                          int ny, float land_depth, unsigned char *land_out,
+                                                          float *eta_out, float *Hm_out) {
+    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i >= nx || j >= ny) return;
+    erode_cell(land, eta, Hm, pitch, nx, ny, land_depth, i, j, land_out, eta_out, Hm_out);
+}
+
+// The same step, four consecutive cells per thread with vector loads and
+// stores (pitch a multiple of 4, float planes 16-byte and byte planes
+// 4-byte aligned): five byte-plane loads and two float4 loads for four
+// cells instead of twenty-eight scalar loads. The same selections and the
+// same order of maxima as erode_cell, so the same bits.
+__global__ void __launch_bounds__(kBX * kBY) erode4_kernel(const unsigned char *land, const float *eta,
+                                                           const float *Hm, long long pitch, int nx,
+                                                           int ny, float land_depth, unsigned char *land_out,
+                                                           float *eta_out, float *Hm_out) {
+    const int i0 = 4 * (blockIdx.x * kBX + threadIdx.x % kBX);
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i0 >= nx || j >= ny) return;
+    if (i0 + 4 > nx) {                          // the ragged end of a row
+        for (int i = i0; i < nx; i++)
+            erode_cell(land, eta, Hm, pitch, nx, ny, land_depth, i, j, land_out, eta_out, Hm_out);
+        return;
+    }
+    const long long s = (long long)j * pitch + i0;
+    const uchar4 one = make_uchar4(1, 1, 1, 1);
+    const uchar4 L = *reinterpret_cast<const uchar4 *>(land + s);
+    const uchar4 LS = j > 0 ? *reinterpret_cast<const uchar4 *>(land + s - pitch) : one;
+    const uchar4 LN = j < ny - 1 ? *reinterpret_cast<const uchar4 *>(land + s + pitch) : one;
+    const bool lW = i0 == 0 || land[s - 1] != 0;
+    const bool lE = i0 + 4 >= nx || land[s + 4] != 0;
+    const float4 E = *reinterpret_cast<const float4 *>(eta + s);
+    const float4 D = *reinterpret_cast<const float4 *>(Hm + s);
+    const bool l[4] = {L.x != 0, L.y != 0, L.z != 0, L.w != 0};
+    const bool ls[4] = {LS.x != 0, LS.y != 0, LS.z != 0, LS.w != 0};
+    const bool ln[4] = {LN.x != 0, LN.y != 0, LN.z != 0, LN.w != 0};
+    const float ein[4] = {E.x, E.y, E.z, E.w};
+    float e[4] = {E.x, E.y, E.z, E.w}, h[4] = {D.x, D.y, D.z, D.w};
+    unsigned char stay[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const bool lw = k == 0 ? lW : l[k - 1], le = k == 3 ? lE : l[k + 1];
+        const bool stays = l[k] && lw && le && ls[k] && ln[k];
+        if (l[k] && !stays) {
+            float m = -INFINITY;
+            if (!lw) m = fmaxf(m, k == 0 ? eta[s - 1] : ein[k - 1]);
+            if (!le) m = fmaxf(m, k == 3 ? eta[s + 4] : ein[k + 1]);
+            if (!ls[k]) m = fmaxf(m, eta[s + k - pitch]);
+            if (!ln[k]) m = fmaxf(m, eta[s + k + pitch]);
+            e[k] = m;
+            h[k] = land_depth;
+        }
+        stay[k] = stays ? 1 : 0;
+    }
+    *reinterpret_cast<uchar4 *>(land_out + s) = make_uchar4(stay[0], stay[1], stay[2], stay[3]);
+    *reinterpret_cast<float4 *>(eta_out + s) = make_float4(e[0], e[1], e[2], e[3]);
+    *reinterpret_cast<float4 *>(Hm_out + s) = make_float4(h[0], h[1], h[2], h[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,8 +498,14 @@ int swe_land_erode(const unsigned char *land, const float *eta, const float *Hm,
     if ((const void *)land_out == (const void *)land || eta_out == eta || Hm_out == Hm)
         return SWE_ERR_INVALID_ARG;
     if (!(land_depth >= 0.0)) return SWE_ERR_INVALID_ARG;
-    erode_kernel<<<grid_for(nx, ny), kBX * kBY, 0, (cudaStream_t)stream>>>(
-        land, eta, Hm, pitch, nx, ny, (float)land_depth, land_out, eta_out, Hm_out);
+    auto al = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
+    if (pitch % 4 == 0 && al(land, 4) && al(land_out, 4) && al(eta, 16) && al(Hm, 16) && al(eta_out, 16) &&
+        al(Hm_out, 16))
+        erode4_kernel<<<grid_for(((long long)nx + 3) / 4, ny), kBX * kBY, 0, (cudaStream_t)stream>>>(
+            land, eta, Hm, pitch, nx, ny, (float)land_depth, land_out, eta_out, Hm_out);
+    else
+        erode_kernel<<<grid_for(nx, ny), kBX * kBY, 0, (cudaStream_t)stream>>>(
+            land, eta, Hm, pitch, nx, ny, (float)land_depth, land_out, eta_out, Hm_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SWE_OK : prep_fail(e);
 }

@@ -94,13 +94,18 @@ def test_bathymetry_full_size_4096():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("nx,ny", [(64, 48), (1, 7), (130, 3), (8192, 64)])
-def test_land_erosion_is_bit_exact(nx, ny):
+@pytest.mark.parametrize("aligned", [False, True])
+@pytest.mark.parametrize("nx,ny", [(64, 48), (1, 7), (130, 3), (67, 33), (8192, 64)])
+def test_land_erosion_is_bit_exact(nx, ny, aligned):
+    """Both kernels: one cell per thread (a pitch that is not a multiple of
+    4) and four cells per thread with vector loads (pitch a multiple of 4;
+    a row length that is not is finished cell by cell)."""
     rng = np.random.default_rng(nx + 17 * ny)
     land = rng.random((ny, nx)) < 0.5
     eta = rng.standard_normal((ny, nx)).astype(np.float32)
     Hm = rng.uniform(5.0, 300.0, (ny, nx)).astype(np.float32)
-    pad = 6
+    pad = 8 - nx % 4 if aligned else (6 if (nx + 6) % 4 else 5)
+    assert ((nx + pad) % 4 == 0) == aligned
     L_d = _dev(land.astype(np.uint8), np.uint8, pad)
     e_d, H_d = _dev(eta, np.float32, pad), _dev(Hm, np.float32, pad)
     Lo, eo, Ho = torch.zeros_like(L_d), torch.zeros_like(e_d), torch.zeros_like(H_d)
