@@ -336,12 +336,24 @@ struct OutPlanes3 {
     float *q[3];
 };
 
-__global__ void __launch_bounds__(kBX * kBY) refine_cells_kernel(Planes3 in, long long pitch, const float *H,
-                                                                 long long cp, int nx, int ny, float theta,
-                                                                 OutPlanes3 out, long long fp) {
-    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
-    if (i >= nx || j >= ny) return;
+// The four children of a water cell with value c and one-sided
+// differences bx, fx (x) and by, fy (y): limited slopes, children at
+// x +- 1/4, y +- 1/4 of the cell (lo: the lower row of children).
+__device__ __forceinline__ void refine_children(float c, float bx, float fx, float by, float fy, float theta,
+                                                float2 &lo, float2 &hi) {
+    const float sx = gminmod(theta * bx, 0.5f * (bx + fx), theta * fx);
+    const float sy = gminmod(theta * by, 0.5f * (by + fy), theta * fy);
+    lo.x = (c - 0.25f * sx) - 0.25f * sy;
+    lo.y = (c + 0.25f * sx) - 0.25f * sy;
+    hi.x = (c - 0.25f * sx) + 0.25f * sy;
+    hi.y = (c + 0.25f * sx) + 0.25f * sy;
+}
+
+// One coarse cell (i, j) of the refinement (the one-cell kernel, and the odd
+// last cell of a row in the two-cell kernel).
+__device__ __forceinline__ void refine_cell(const Planes3 &in, long long pitch, const float *H, long long cp,
+                                            int nx, int ny, float theta, const OutPlanes3 &out, long long fp,
+                                            int i, int j) {
     const bool land = corner_land(H, cp, j, i);
     // a neighbour that is land or outside gives a zero one-sided difference
     const bool nw = i > 0 && !corner_land(H, cp, j, i - 1);
@@ -355,18 +367,83 @@ __global__ void __launch_bounds__(kBX * kBY) refine_cells_kernel(Planes3 in, lon
         if (!land) {
             const float *p = in.q[v] + s;
             const float c = p[0];
-            const float bx = nw ? c - p[-1] : 0.f, fx = ne ? p[1] - c : 0.f;
-            const float by = ns ? c - p[-pitch] : 0.f, fy = nn ? p[pitch] - c : 0.f;
-            const float sx = gminmod(theta * bx, 0.5f * (bx + fx), theta * fx);
-            const float sy = gminmod(theta * by, 0.5f * (by + fy), theta * fy);
-            // children at x +- 1/4, y +- 1/4 of the cell
-            lo.x = (c - 0.25f * sx) - 0.25f * sy;
-            lo.y = (c + 0.25f * sx) - 0.25f * sy;
-            hi.x = (c - 0.25f * sx) + 0.25f * sy;
-            hi.y = (c + 0.25f * sx) + 0.25f * sy;
+            refine_children(c, nw ? c - p[-1] : 0.f, ne ? p[1] - c : 0.f, ns ? c - p[-pitch] : 0.f,
+                            nn ? p[pitch] - c : 0.f, theta, lo, hi);
         }
         *reinterpret_cast<float2 *>(out.q[v] + f0) = lo;
         *reinterpret_cast<float2 *>(out.q[v] + f0 + fp) = hi;
+    }
+}
+
+__global__ void __launch_bounds__(kBX * kBY) refine_cells_kernel(Planes3 in, long long pitch, const float *H,
+                                                                 long long cp, int nx, int ny, float theta,
+                                                                 OutPlanes3 out, long long fp) {
+    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i >= nx || j >= ny) return;
+    refine_cell(in, pitch, H, cp, nx, ny, theta, out, fp, i, j);
+}
+
+// The same refinement, two coarse cells (i0, i0 + 1) per thread (coarse
+// pitch even and coarse planes 8-byte aligned; fine pitch a multiple of 4
+// and fine planes 16-byte aligned): float2 loads of the cells and their
+// y-neighbours, the land of the six cells around them from one read of
+// their corners, and one float4 store per row of children. The same
+// selections and arithmetic as refine_cell, so the same bits.
+__global__ void __launch_bounds__(kBX * kBY) refine2_cells_kernel(Planes3 in, long long pitch, const float *H,
+                                                                  long long cp, int nx, int ny, float theta,
+                                                                  OutPlanes3 out, long long fp) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x % kBX);
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i0 >= nx || j >= ny) return;
+    if (i0 + 1 >= nx) {                          // the odd last cell of a row
+        refine_cell(in, pitch, H, cp, nx, ny, theta, out, fp, i0, j);
+        return;
+    }
+    // corners of rows j, j + 1 at columns i0 - 1 .. i0 + 3 (where they exist)
+    const float *c = H + (long long)j * cp + i0;
+    const bool has_w = i0 > 0, has_e = i0 + 2 < nx, has_s = j > 0, has_n = j < ny - 1;
+    bool a[5], b[5];                             // corner is LAND, rows j and j + 1
+#pragma unroll
+    for (int x = 0; x < 5; x++) {
+        const bool ok = (x > 0 || has_w) && (x < 4 || has_e);
+        a[x] = ok && c[x - 1] == kLand;
+        b[x] = ok && c[cp + x - 1] == kLand;
+    }
+    const bool landW = a[0] | a[1] | b[0] | b[1], land0 = a[1] | a[2] | b[1] | b[2];
+    const bool land1 = a[2] | a[3] | b[2] | b[3], landE = a[3] | a[4] | b[3] | b[4];
+    bool landS0 = true, landS1 = true, landN0 = true, landN1 = true;
+    if (has_s) {
+        const float *d = c - cp;
+        const bool s0 = d[0] == kLand, s1 = d[1] == kLand, s2 = d[2] == kLand;
+        landS0 = s0 | s1 | a[1] | a[2];
+        landS1 = s1 | s2 | a[2] | a[3];
+    }
+    if (has_n) {
+        const float *d = c + 2 * cp;
+        const bool n0 = d[0] == kLand, n1 = d[1] == kLand, n2 = d[2] == kLand;
+        landN0 = b[1] | b[2] | n0 | n1;
+        landN1 = b[2] | b[3] | n1 | n2;
+    }
+    const bool nw0 = has_w && !landW, ne0 = !land1, ns0 = has_s && !landS0, nn0 = has_n && !landN0;
+    const bool nw1 = !land0, ne1 = has_e && !landE, ns1 = has_s && !landS1, nn1 = has_n && !landN1;
+    const long long s = (long long)j * pitch + i0;
+    const long long f0 = (long long)(2 * j) * fp + 2 * i0;
+    for (int v = 0; v < 3; v++) {
+        const float *p = in.q[v] + s;
+        const float2 P = *reinterpret_cast<const float2 *>(p);
+        const float pw = has_w ? p[-1] : 0.f, pe = has_e ? p[2] : 0.f;
+        const float2 S = has_s ? *reinterpret_cast<const float2 *>(p - pitch) : make_float2(0.f, 0.f);
+        const float2 N = has_n ? *reinterpret_cast<const float2 *>(p + pitch) : make_float2(0.f, 0.f);
+        float2 lo0 = make_float2(0.f, 0.f), hi0 = lo0, lo1 = lo0, hi1 = lo0;
+        if (!land0)
+            refine_children(P.x, nw0 ? P.x - pw : 0.f, ne0 ? P.y - P.x : 0.f, ns0 ? P.x - S.x : 0.f,
+                            nn0 ? N.x - P.x : 0.f, theta, lo0, hi0);
+        if (!land1)
+            refine_children(P.y, nw1 ? P.y - P.x : 0.f, ne1 ? pe - P.y : 0.f, ns1 ? P.y - S.y : 0.f,
+                            nn1 ? N.y - P.y : 0.f, theta, lo1, hi1);
+        *reinterpret_cast<float4 *>(out.q[v] + f0) = make_float4(lo0.x, lo0.y, lo1.x, lo1.y);
+        *reinterpret_cast<float4 *>(out.q[v] + f0 + fp) = make_float4(hi0.x, hi0.y, hi1.x, hi1.y);
     }
 }
 
@@ -524,8 +601,14 @@ int swe_refine2(const float *eta, const float *hu, const float *hv, long long pi
     cudaStream_t st = (cudaStream_t)stream;
     Planes3 in{{eta, hu, hv}};
     OutPlanes3 out{{eta_f, hu_f, hv_f}};
-    refine_cells_kernel<<<grid_for(nx, ny), kBX * kBY, 0, st>>>(in, pitch, H, cpitch, nx, ny, (float)theta,
-                                                                out, fpitch);
+    auto al = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
+    if (pitch % 2 == 0 && fpitch % 4 == 0 && al(eta, 8) && al(hu, 8) && al(hv, 8) && al(eta_f, 16) &&
+        al(hu_f, 16) && al(hv_f, 16))
+        refine2_cells_kernel<<<grid_for(((long long)nx + 1) / 2, ny), kBX * kBY, 0, st>>>(
+            in, pitch, H, cpitch, nx, ny, (float)theta, out, fpitch);
+    else
+        refine_cells_kernel<<<grid_for(nx, ny), kBX * kBY, 0, st>>>(in, pitch, H, cpitch, nx, ny, (float)theta,
+                                                                    out, fpitch);
     refine_corners_kernel<<<grid_for(nx + 1, ny + 1), kBX * kBY, 0, st>>>(H, cpitch, nx, ny, H_f, fcpitch);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SWE_OK : prep_fail(e);

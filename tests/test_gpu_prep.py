@@ -126,11 +126,15 @@ def _coastal_small(nx, ny, seed):
     return q, wl.H.astype(np.float32)
 
 
-def _refine_gpu(q, H, nx, ny):
+def _refine_gpu(q, H, nx, ny, vec=False):
+    """vec: an even coarse pitch and a fine pitch that is a multiple of 4
+    (the two-cell kernel with vector loads and stores); else an odd coarse
+    pitch (the one-cell kernel)."""
     st = torch.cuda.current_stream().cuda_stream
-    qd = [_dev(a, np.float32, pad=5) for a in q]
+    qd = [_dev(a, np.float32, pad=4 + nx % 2 if vec else 5 - nx % 2) for a in q]
+    assert (qd[0].stride(0) % 2 == 0) == vec
     Hd = _dev(H, np.float32, pad=3)
-    fp, fcp = 2 * nx + 4, 2 * nx + 3
+    fp, fcp = (2 * nx + 4 + 3) // 4 * 4 if vec else 2 * nx + 4, 2 * nx + 3
     qf = [torch.zeros((2 * ny, fp), dtype=torch.float32, device="cuda") for _ in range(3)]
     Hf = torch.zeros((2 * ny + 1, fcp), dtype=torch.float32, device="cuda")
     swe.refine2([t.data_ptr() for t in qd], qd[0].stride(0), Hd.data_ptr(), Hd.stride(0), nx, ny,
@@ -138,13 +142,30 @@ def _refine_gpu(q, H, nx, ny):
     return qf, Hf, fp, fcp
 
 
-@pytest.mark.gpu
-@pytest.mark.parametrize("nx,ny", [(70, 46), (33, 9), (1, 1), (2, 5)])
-def test_refine_and_coarsen_match_oracle(nx, ny):
-    q, H = _coastal_small(nx, ny, nx + ny) if min(nx, ny) > 4 else (
+def _small_case(nx, ny):
+    return _coastal_small(nx, ny, nx + ny) if min(nx, ny) > 4 else (
         [np.random.default_rng(3).standard_normal((ny, nx)).astype(np.float32) for _ in range(3)],
         np.random.default_rng(4).uniform(5, 50, (ny + 1, nx + 1)).astype(np.float32))
-    qf, Hf, fp, fcp = _refine_gpu(q, H, nx, ny)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny", [(70, 46), (33, 9), (1, 1), (2, 5), (257, 31)])
+def test_refine_kernels_agree_bitwise(nx, ny):
+    """The two-cell kernel (vector loads and stores, odd last cell of a row
+    by the one-cell code) gives the one-cell kernel's bits."""
+    q, H = _small_case(nx, ny)
+    a, _, _, _ = _refine_gpu(q, H, nx, ny, vec=False)
+    b, _, _, _ = _refine_gpu(q, H, nx, ny, vec=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(_host(x, 2 * nx), _host(y, 2 * nx))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("vec", [False, True])
+@pytest.mark.parametrize("nx,ny", [(70, 46), (33, 9), (1, 1), (2, 5)])
+def test_refine_and_coarsen_match_oracle(nx, ny, vec):
+    q, H = _small_case(nx, ny)
+    qf, Hf, fp, fcp = _refine_gpu(q, H, nx, ny, vec=vec)
     ref = prep.refine2(*(a.astype(np.float64) for a in q), H.astype(np.float64))
     scale = max(float(np.abs(np.stack(q)).max()), 1e-30)
     for t, r in zip(qf, ref[:3]):
@@ -176,7 +197,7 @@ def test_refine_and_coarsen_match_oracle(nx, ny):
 def test_refine_full_size_4096_sampled():
     nx = ny = 4096
     q, H = _coastal_small(nx, ny, 9)
-    qf, Hf, fp, fcp = _refine_gpu(q, H, nx, ny)
+    qf, Hf, fp, fcp = _refine_gpu(q, H, nx, ny, vec=True)    # the layout the bench times
     # sampled rows against the oracle on the slab of rows j-1..j+1 that
     # decides them (a slab edge is a domain edge only where it is one)
     rng = np.random.default_rng(0)
