@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <queue>
 #include <vector>
 
 #include "swe_device.cuh"
@@ -719,7 +720,7 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
                std::vector<uint2> &items) {
     items.clear();
     const PlanCtx p = plan_ctx(nx, ny, wet, bc, frs_width);
-    std::vector<long long> pref;
+    std::vector<long long> pref, cost;
     for (const Segment &g : plan_segments(p)) {
         const int xs = p.strip_extra(g.strip);
         pref.assign((size_t)g.rows + 1, 0);
@@ -737,16 +738,38 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
                 if (r1 - 1 > r0 && target - pref[r1 - 1] < pref[r1] - target) r1--;
             }
             items.push_back(make_uint2((unsigned)g.strip, (unsigned)(g.start + r0) | ((unsigned)(r1 - r0) << 16)));
+            cost.push_back(pref[r1] - pref[r0] + kHaloCost);
             r0 = r1;
         }
     }
-    if (items.empty()) items.push_back(make_uint2(0u, 1u << 16));   // all land: a no-op item runs the clock
-    // row-major order: a block's warps take neighbouring strips of the same
-    // rows (they share halo lines in L1), and every SM gets a mix of strips
-    std::sort(items.begin(), items.end(), [](const uint2 &a, const uint2 &b) {
-        const unsigned ja = a.y & 0xffffu, jb = b.y & 0xffffu;
-        return ja != jb ? ja < jb : a.x < b.x;
-    });
+    if (items.empty()) { items.push_back(make_uint2(0u, 1u << 16)); cost.push_back(1); }
+    // blocks of kWarps items with equal total cost (largest item first to
+    // the lightest block with room), so that the SMs, whichever blocks they
+    // get, carry equal work; within a block, row-major order
+    const int n = (int)items.size(), nb = (n + kWarps - 1) / kWarps;
+    std::vector<int> order(n);
+    for (int k = 0; k < n; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    typedef std::pair<long long, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < nb; b++) heap.push(Load(0, b));
+    std::vector<std::vector<int>> blk(nb);
+    for (int k : order) {
+        Load l = heap.top();
+        heap.pop();
+        blk[l.second].push_back(k);
+        if ((int)blk[l.second].size() < kWarps) heap.push(Load(l.first + cost[k], l.second));
+    }
+    std::vector<uint2> out;
+    out.reserve(n);
+    for (int b = 0; b < nb; b++) {
+        std::sort(blk[b].begin(), blk[b].end(), [&](int a, int c) {
+            const unsigned ja = items[a].y & 0xffffu, jc = items[c].y & 0xffffu;
+            return ja != jc ? ja < jc : items[a].x < items[c].x;
+        });
+        for (int k : blk[b]) out.push_back(items[k]);
+    }
+    items.swap(out);
 }
 
 int fast_step_parts() { return 2; }
