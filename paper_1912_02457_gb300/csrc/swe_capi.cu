@@ -96,7 +96,7 @@ struct swe_domain {
     // destroyed (captured graphs and batch tables point at them)
     std::vector<unsigned char> wet;
     int budget = 0;
-    struct ItemList { int budget, n; uint2 *dev; };
+    struct ItemList { int budget; bool alone; int n; uint2 *dev; };
     std::vector<ItemList> item_lists;
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
@@ -215,15 +215,16 @@ int ensure_wet(swe_domain *d) {
     return SWE_OK;
 }
 
-// The device plan of the fast path for a work budget (built once).
-int domain_items(swe_domain *d, int budget, const uint2 **dev, int *n) {
+// The device plan of the fast path for a work budget, for the domain
+// launched alone or in a batch (built once).
+int domain_items(swe_domain *d, int budget, bool alone, const uint2 **dev, int *n) {
     for (const auto &l : d->item_lists)
-        if (l.budget == budget) { *dev = l.dev; *n = l.n; return SWE_OK; }
+        if (l.budget == budget && l.alone == alone) { *dev = l.dev; *n = l.n; return SWE_OK; }
     int rc = ensure_wet(d);
     if (rc) return rc;
     std::vector<uint2> items;
     try {
-        swe::fast_plan(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width, budget, items);
+        swe::fast_plan(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width, budget, alone, items);
     } catch (...) {
         return SWE_ERR_OOM;
     }
@@ -233,7 +234,7 @@ int domain_items(swe_domain *d, int budget, const uint2 **dev, int *n) {
                                     d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) { d->dfree(p); return cuda_fail(e); }
-    d->item_lists.push_back({budget, (int)items.size(), p});
+    d->item_lists.push_back({budget, alone, (int)items.size(), p});
     *dev = p;
     *n = (int)items.size();
     return SWE_OK;
@@ -241,10 +242,10 @@ int domain_items(swe_domain *d, int budget, const uint2 **dev, int *n) {
 
 // Arguments of the fast path for a work budget, its plan and the blocks a
 // launch over it takes.
-int fast_args(swe_domain *d, int budget, StageArgs<float> *a, int *tiles) {
+int fast_args(swe_domain *d, int budget, bool alone, StageArgs<float> *a, int *tiles) {
     const uint2 *items = nullptr;
     int n = 0;
-    int rc = domain_items(d, budget, &items, &n);
+    int rc = domain_items(d, budget, alone, &items, &n);
     if (rc) return rc;
     *a = make_args<float>(d);
     a->items = items;
@@ -262,7 +263,7 @@ int upload_table(swe_domain *d) {
     if (!d->budget) d->budget = swe::fast_budget(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width);
     d->one.rows = d->budget / swe::kPlanUnit;
     d->one.strips = swe::fast_strips(d->nx);
-    return fast_args(d, d->budget, &d->one.args, &d->one.tiles);
+    return fast_args(d, d->budget, true, &d->one.args, &d->one.tiles);
 }
 
 int upload_plane(swe_domain *d, void *dst, const void *src, int rows, int cols,
@@ -751,7 +752,7 @@ int batch_upload(swe_batch *b) {
     for (int k = 0; k < n; k++) {
         rows[k] = b->budget[k] / swe::kPlanUnit;
         int tiles = 0;
-        int rc = fast_args(b->doms[k], b->budget[k], &args[k], &tiles);
+        int rc = fast_args(b->doms[k], b->budget[k], false, &args[k], &tiles);
         if (rc) return rc;
         gx[k] = swe::fast_strips(b->doms[k]->nx);
         start[k + 1] = start[k] + tiles;

@@ -38,8 +38,9 @@ const char *fast_part_name(int part);
 constexpr int kPlanUnit = 100;
 int fast_strips(int nx);
 int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width);
+// alone: the plan of a domain launched by itself (a batch launches many)
 void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width, int budget,
-               std::vector<uint2> &items);
+               bool alone, std::vector<uint2> &items);
 int fast_tiles(int n_items);
 cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
                               cudaStream_t st);

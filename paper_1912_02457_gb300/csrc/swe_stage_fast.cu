@@ -717,7 +717,7 @@ int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int f
 }
 
 void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width, int budget,
-               std::vector<uint2> &items) {
+               bool alone, std::vector<uint2> &items) {
     items.clear();
     const PlanCtx p = plan_ctx(nx, ny, wet, bc, frs_width);
     std::vector<long long> pref, cost;
@@ -743,12 +743,30 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
         }
     }
     if (items.empty()) { items.push_back(make_uint2(0u, 1u << 16)); cost.push_back(1); }
-    // blocks of kWarps items with equal total cost (largest item first to
-    // the lightest block with room), so that the SMs, whichever blocks they
-    // get, carry equal work; within a block, row-major order
     const int n = (int)items.size(), nb = (n + kWarps - 1) / kWarps;
+    const auto row_major = [&](int a, int c) {
+        const unsigned ja = items[a].y & 0xffffu, jc = items[c].y & 0xffffu;
+        return ja != jc ? ja < jc : items[a].x < items[c].x;
+    };
     std::vector<int> order(n);
     for (int k = 0; k < n; k++) order[k] = k;
+    std::vector<uint2> out;
+    out.reserve(n);
+    if (!alone || n > warp_slots() || budget < 8 * kPlanUnit) {
+        // part of a batch, several waves, or short items: row-major order,
+        // a block's warps
+        // taking neighbouring strips of the same rows (they share halo lines
+        // in L1, which short items and later waves depend on; measured
+        // 1-2% faster than balanced blocks there)
+        std::sort(order.begin(), order.end(), row_major);
+        for (int k : order) out.push_back(items[k]);
+        items.swap(out);
+        return;
+    }
+    // one wave of long items: blocks of kWarps items with equal total cost
+    // (largest item first to the lightest block with room), so that the SMs,
+    // whichever blocks they get, carry equal work (coastal 1024^2: +2.6%);
+    // within a block, row-major order
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     typedef std::pair<long long, int> Load;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
@@ -760,13 +778,8 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
         blk[l.second].push_back(k);
         if ((int)blk[l.second].size() < kWarps) heap.push(Load(l.first + cost[k], l.second));
     }
-    std::vector<uint2> out;
-    out.reserve(n);
     for (int b = 0; b < nb; b++) {
-        std::sort(blk[b].begin(), blk[b].end(), [&](int a, int c) {
-            const unsigned ja = items[a].y & 0xffffu, jc = items[c].y & 0xffffu;
-            return ja != jc ? ja < jc : items[a].x < items[c].x;
-        });
+        std::sort(blk[b].begin(), blk[b].end(), row_major);
         for (int k : blk[b]) out.push_back(items[k]);
     }
     items.swap(out);
