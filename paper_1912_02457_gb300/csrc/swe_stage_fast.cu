@@ -456,7 +456,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
                                            int nblocks, const bool KAHAN) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    if (a.ctl->done) return;                       // forecast horizon reached (block-uniform)
+    // the clock state and the warp's item are loaded together (one round
+    // trip to memory before the march), then the horizon is checked
+    const StepCtl *ctl = a.ctl;
+    const int done = ctl->done, par = ctl->parity;
+    const double dt = ctl->dt;
+    const float taux = ctl->tau_f[STAGE - 1][0], tauy = ctl->tau_f[STAGE - 1][1];
     // warp slot -> warp item: from the domain's plan, or (without one) the
     // item-th strip of `rows`-row bands
     const int slot = blk * kWarps + warp;
@@ -475,12 +480,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         strip_live = slot < strips * bands;
         if (strip_live) { strip = slot % strips; j0 = slot / strips * rows; j1 = min(j0 + rows, a.ny); }
     }
+    if (done) return;                              // forecast horizon reached (block-uniform)
     StripCtx k;
     k.lane = lane;
     k.i = strip * kStrip - 2 + lane;
     k.j0 = j0;
     k.j1 = j1;
-    k.par = a.ctl->parity;
+    k.par = par;
     // stage 1 also evaluates the external edge state of the next time level
     // (used by stage 2 and by stage 1 of the next step); the interior
     // blocks of the middle of the domain take it
@@ -489,12 +495,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         edge_fill(a, k.par ^ 1, 1, b * (kWarps * 32) + threadIdx.x, nblocks * (kWarps * 32));
     }
     k.out_lane = lane >= 2 && lane < 2 + kStrip && k.i < a.nx;
-    k.dt = (float)a.ctl->dt;
+    k.dt = (float)dt;
     k.rho_ratio = (float)a.clk.rho_ratio;
     k.wind_on = a.wind.n > 0;
     k.wind_uni = a.clk.wind_uniform != 0;
-    k.taux = a.ctl->tau_f[STAGE - 1][0];
-    k.tauy = a.ctl->tau_f[STAGE - 1][1];
+    k.taux = taux;
+    k.tauy = tauy;
     // does any cell of this warp's strip lie in a flow-relaxation zone?
     {
         const int c0 = strip * kStrip, c1 = c0 + kStrip, fw = a.frs_width;
