@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kBX * kBY) residual_kernel(const float *Hm, lo
 //      extrapolated beyond an edge); the initial guess is T as it stands.
 // The misfit max|dH| of X and the largest change max|Y - X| go to misfit
 // and change.
-constexpr int kTX = 32, kTY = 16, kTileThreads = 256;
+constexpr int kTX = 64, kTY = 32, kTileThreads = 256;
 
 __global__ void __launch_bounds__(kTileThreads) bathy_tile_kernel(const float *Hm, long long pitch, int nx,
                                                                   int ny, const float *X, long long xp,
@@ -473,12 +473,10 @@ __global__ void __launch_bounds__(kBX * kBY) refine_corners_kernel(const float *
     }
 }
 
-__global__ void __launch_bounds__(kBX * kBY) coarsen_cells_kernel(Planes3 fin, long long fp, const float *Hf,
-                                                                  long long fcp, int nx, int ny, OutPlanes3 out,
-                                                                  long long pitch) {
-    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
-    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
-    if (i >= nx || j >= ny) return;
+// One coarse cell (i, j) of the coarsening (the one-cell kernel, and the odd
+// last cell of a row in the two-cell kernel).
+__device__ __forceinline__ void coarsen_cell(const Planes3 &fin, long long fp, const float *Hf, long long fcp,
+                                             const OutPlanes3 &out, long long pitch, int i, int j) {
     // the coarse cell is land if one of its sampled corners is
     const float *cc = Hf + (long long)(2 * j) * fcp + 2 * i;
     const bool cland = (cc[0] == kLand) | (cc[2] == kLand) | (cc[2 * fcp] == kLand) | (cc[2 * fcp + 2] == kLand);
@@ -496,6 +494,66 @@ __global__ void __launch_bounds__(kBX * kBY) coarsen_cells_kernel(Planes3 fin, l
         const float s = (((wet[0] ? lo.x : 0.f) + (wet[1] ? lo.y : 0.f)) + (wet[2] ? hi.x : 0.f)) +
                         (wet[3] ? hi.y : 0.f);
         out.q[v][(long long)j * pitch + i] = (cland || n_wet == 0.f) ? 0.f : s / n_wet;
+    }
+}
+
+__global__ void __launch_bounds__(kBX * kBY) coarsen_cells_kernel(Planes3 fin, long long fp, const float *Hf,
+                                                                  long long fcp, int nx, int ny, OutPlanes3 out,
+                                                                  long long pitch) {
+    const int i = blockIdx.x * kBX + threadIdx.x % kBX;
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i >= nx || j >= ny) return;
+    coarsen_cell(fin, fp, Hf, fcp, out, pitch, i, j);
+}
+
+// The same coarsening, two coarse cells (i0, i0 + 1) per thread (fine pitch
+// a multiple of 4 and fine planes 16-byte aligned; coarse pitch even and
+// coarse planes 8-byte aligned): one read of the 3 x 5 fine corners they
+// share, float4 loads of the children, one float2 store per plane. The same
+// selections and arithmetic as coarsen_cell, so the same bits.
+__global__ void __launch_bounds__(kBX * kBY) coarsen2_cells_kernel(Planes3 fin, long long fp, const float *Hf,
+                                                                   long long fcp, int nx, int ny, OutPlanes3 out,
+                                                                   long long pitch) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x % kBX);
+    const int j = blockIdx.y * kBY + threadIdx.x / kBX;
+    if (i0 >= nx || j >= ny) return;
+    if (i0 + 1 >= nx) {                          // the odd last cell of a row
+        coarsen_cell(fin, fp, Hf, fcp, out, pitch, i0, j);
+        return;
+    }
+    // fine corners of rows 2j .. 2j + 2, columns 2 i0 .. 2 i0 + 4: LAND?
+    const float *cc = Hf + (long long)(2 * j) * fcp + 2 * i0;
+    bool L[3][5];
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int x = 0; x < 5; x++) L[b][x] = cc[b * fcp + x] == kLand;
+    bool cland[2], wet[2][4];
+    float n_wet[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        cland[k] = L[0][2 * k] | L[0][2 * k + 2] | L[2][2 * k] | L[2][2 * k + 2];
+        n_wet[k] = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const int x = 2 * k + a;
+                wet[k][2 * b + a] = !(L[b][x] | L[b][x + 1] | L[b + 1][x] | L[b + 1][x + 1]);
+                n_wet[k] += wet[k][2 * b + a] ? 1.f : 0.f;
+            }
+    }
+    const long long f0 = (long long)(2 * j) * fp + 2 * i0;
+    for (int v = 0; v < 3; v++) {
+        const float4 lo = *reinterpret_cast<const float4 *>(fin.q[v] + f0);
+        const float4 hi = *reinterpret_cast<const float4 *>(fin.q[v] + f0 + fp);
+        const float s0 = (((wet[0][0] ? lo.x : 0.f) + (wet[0][1] ? lo.y : 0.f)) + (wet[0][2] ? hi.x : 0.f)) +
+                         (wet[0][3] ? hi.y : 0.f);
+        const float s1 = (((wet[1][0] ? lo.z : 0.f) + (wet[1][1] ? lo.w : 0.f)) + (wet[1][2] ? hi.z : 0.f)) +
+                         (wet[1][3] ? hi.w : 0.f);
+        *reinterpret_cast<float2 *>(out.q[v] + (long long)j * pitch + i0) =
+            make_float2((cland[0] || n_wet[0] == 0.f) ? 0.f : s0 / n_wet[0],
+                        (cland[1] || n_wet[1] == 0.f) ? 0.f : s1 / n_wet[1]);
     }
 }
 
@@ -626,7 +684,14 @@ int swe_coarsen2(const float *eta_f, const float *hu_f, const float *hv_f, long 
     cudaStream_t st = (cudaStream_t)stream;
     Planes3 fin{{eta_f, hu_f, hv_f}};
     OutPlanes3 out{{eta, hu, hv}};
-    coarsen_cells_kernel<<<grid_for(nx, ny), kBX * kBY, 0, st>>>(fin, fpitch, H_f, fcpitch, nx, ny, out, pitch);
+    auto al = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
+    if (fpitch % 4 == 0 && pitch % 2 == 0 && al(eta_f, 16) && al(hu_f, 16) && al(hv_f, 16) && al(eta, 8) &&
+        al(hu, 8) && al(hv, 8))
+        coarsen2_cells_kernel<<<grid_for(((long long)nx + 1) / 2, ny), kBX * kBY, 0, st>>>(
+            fin, fpitch, H_f, fcpitch, nx, ny, out, pitch);
+    else
+        coarsen_cells_kernel<<<grid_for(nx, ny), kBX * kBY, 0, st>>>(fin, fpitch, H_f, fcpitch, nx, ny, out,
+                                                                     pitch);
     coarsen_corners_kernel<<<grid_for(nx + 1, ny + 1), kBX * kBY, 0, st>>>(H_f, fcpitch, nx, ny, H, cpitch);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SWE_OK : prep_fail(e);

@@ -161,6 +161,27 @@ def test_refine_kernels_agree_bitwise(nx, ny):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny", [(70, 46), (33, 9), (1, 1), (2, 5), (257, 31)])
+def test_coarsen_kernels_agree_bitwise(nx, ny):
+    """The two-cell coarsening kernel (fine pitch a multiple of 4, even
+    coarse pitch; the odd last cell of a row by the one-cell code) gives the
+    one-cell kernel's bits."""
+    q, H = _small_case(nx, ny)
+    qf, Hf, fp, fcp = _refine_gpu(q, H, nx, ny, vec=True)
+    st = torch.cuda.current_stream().cuda_stream
+    got = []
+    for cpad in (nx % 2 + 2, nx % 2 + 1):          # even, then odd coarse pitch
+        cq = [torch.zeros((ny, nx + cpad), dtype=torch.float32, device="cuda") for _ in range(3)]
+        cH = torch.zeros((ny + 1, nx + 3), dtype=torch.float32, device="cuda")
+        assert (cq[0].stride(0) % 2 == 0) == (cpad == nx % 2 + 2)
+        swe.coarsen2([t.data_ptr() for t in qf], fp, Hf.data_ptr(), fcp, nx, ny,
+                     [t.data_ptr() for t in cq], cq[0].stride(0), cH.data_ptr(), nx + 3, stream=st)
+        got.append([_host(t, nx) for t in cq])
+    for a, b in zip(*got):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("vec", [False, True])
 @pytest.mark.parametrize("nx,ny", [(70, 46), (33, 9), (1, 1), (2, 5)])
 def test_refine_and_coarsen_match_oracle(nx, ny, vec):
