@@ -213,12 +213,13 @@ int swe_destroy_domain(swe_handle h);
 
 /* ---- batches: ensembles and served forecasts --------------------------
  * A batch advances many FP32 domains (of any sizes, each with its own
- * clock, dt, forcing and horizon) by ONE persistent launch per RK stage:
- * every block walks a device-resident table of tiles covering all domains,
- * and each domain's CFL reduction and clock update are done by its own last
- * tile. Runs of 8 batch steps replay one CUDA graph; because the tables,
+ * clock, dt, forcing and horizon) by ONE launch per RK stage: a block per
+ * tile of a device-resident table of tiles covering all domains, and each
+ * domain's CFL reduction and clock update are done by its own last tile.
+ * Runs of 8 batch steps replay one CUDA graph; because the tables,
  * parities, clocks and horizons live on the device, the graph stays valid
- * when domains are added or removed. The result of every domain is bitwise
+ * when domains are added or removed without changing the tile count (it
+ * is recaptured otherwise). The result of every domain is bitwise
  * the same as stepping it alone (the per-cell arithmetic does not depend on
  * the tiling). While in a batch a domain must be stepped only through it;
  * read its state after swe_batch_sync. A domain that reached its end time

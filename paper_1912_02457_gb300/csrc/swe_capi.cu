@@ -88,7 +88,7 @@ struct swe_domain {
     }
 
     // the FP32 fast path: the domain's tiling and arguments, handed to the
-    // persistent stage kernel (the one batches use) with every launch
+    // stage kernel (the one batches use) with every launch
     swe::OneDomain one{};
     // per 28-column strip and row: does it hold a wet cell (the land mask
     // is fixed at creation); the work budget of the domain alone; the
@@ -717,7 +717,7 @@ int swe_destroy_domain(swe_handle h) {
 }  // extern "C"
 
 // ===========================================================================
-// batches: many FP32 domains advanced by one persistent launch per stage
+// batches: many FP32 domains advanced by one launch per stage
 
 struct swe_batch {
     cudaStream_t stream = nullptr;

@@ -91,14 +91,14 @@ struct StageArgs {
     long long n_plane, n_corner, n_edge, n_bnd, n_wind;
 };
 
-// A single FP32 domain handed to the persistent stage kernel with the launch
-// (kernel parameter space): tiles > 0 selects it over the batch table.
+// A single FP32 domain handed to the stage kernel with the launch (kernel
+// parameter space): tiles > 0 selects it over the batch table.
 struct OneDomain {
     StageArgs<float> args;
     int tiles, rows, strips;
 };
 
-// Device-resident tile table of a batch of FP32 domains (persistent kernel).
+// Device-resident tile table of a batch of FP32 domains (one block per tile).
 struct BatchTable {
     const StageArgs<float> *args;   // per domain
     const int *tile_start;          // n+1 prefix sums of tiles per domain

@@ -13,8 +13,9 @@
 //    is two launches and needs no host round trip;
 //  * ghosts of nested edges read an edge-state buffer that stage 1 fills for
 //    the next time level; periodic ghosts read their periodic image;
-//  * one persistent kernel serves single domains (arguments in the launch's
-//    parameter space) and batches (a device tile table);
+//  * one kernel serves single domains (arguments in the launch's parameter
+//    space) and batches (a device tile table), a warp per item of the
+//    domain's work plan;
 //  * this translation unit is built with approximate FP32 reciprocal and
 //    square root (-prec-div=false -prec-sqrt=false): ~2 ulp, far inside the
 //    parity tolerance, and exact zeros stay exact (lake at rest is still

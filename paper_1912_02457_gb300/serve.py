@@ -7,7 +7,7 @@ horizons. The server:
 * admits waiting requests in arrival order whenever their device memory fits
   the budget (each admitted domain keeps its state and forcing resident);
 * advances every admitted domain together in rounds of ``round_steps``
-  batched steps (one persistent launch per RK stage, graph-replayed), each
+  batched steps (one launch per RK stage, graph-replayed), each
   domain on its own clock up to its own horizon;
 * after each round retires the domains that reached their horizon (their
   final state is downloaded to the host) and admits new arrivals, so work

@@ -355,7 +355,7 @@ class Domain:
 
 
 class Batch:
-    """Many FP32 domains advanced by one persistent launch per stage."""
+    """Many FP32 domains advanced by one launch per stage."""
 
     def __init__(self, stream: int = 0, max_domains: int = 4096):
         self._L = load()

@@ -1,5 +1,5 @@
-"""The batched path: many domains of uneven sizes advanced by one persistent
-launch per stage (graph-captured, autotuned tiles). Every domain's result
+"""The batched path: many domains of uneven sizes advanced by one launch per
+stage (graph-captured, autotuned tiles). Every domain's result
 must be bitwise the one it gets alone: the per-cell arithmetic does not
 depend on the tiling, and each domain keeps its own clock and reduction."""
 import numpy as np
