@@ -234,10 +234,13 @@ int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out);
 int swe_batch_add(swe_batch_handle b, swe_handle d);
 int swe_batch_remove(swe_batch_handle b, swe_handle d);
 int swe_batch_size(swe_batch_handle b);
-/* Tile height (rows per warp item; items are 28 columns wide, four to a
- * block). 0 = autotune:
+/* Tile height: the work budget of a warp item in rows (items are 28
+ * columns wide, four to a block; each domain's wet rows are cut into items
+ * of about this cost, land left out). 0 = autotune:
  * the first swe_batch_step of >= 16 steps times 2 steps with each of the
  * heights 8, 16, 32, 64 and keeps the fastest (these are real steps).
+ * Every height a domain is stepped with keeps its work plan (a few bytes
+ * per item) on the device until the domain is destroyed.
  * swe_batch_rows returns the current choice (0 until tuned). */
 int swe_batch_set_rows(swe_batch_handle b, int rows);
 int swe_batch_rows(swe_batch_handle b);
