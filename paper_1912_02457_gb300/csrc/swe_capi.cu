@@ -260,7 +260,13 @@ int upload_table(swe_domain *d) {
     if (!d->fast()) return SWE_OK;
     int rc = ensure_wet(d);
     if (rc) return rc;
-    if (!d->budget) d->budget = swe::fast_budget(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width);
+    if (!d->budget) {
+        try {
+            d->budget = swe::fast_budget(d->nx, d->ny, d->wet.data(), d->bc, d->p.frs_width);
+        } catch (...) {
+            return SWE_ERR_OOM;                     // no exception crosses the C ABI
+        }
+    }
     d->one.rows = d->budget / swe::kPlanUnit;
     d->one.strips = swe::fast_strips(d->nx);
     return fast_args(d, d->budget, true, &d->one.args, &d->one.tiles);
@@ -745,7 +751,18 @@ namespace {
 
 const int kTuneRows[] = {8, 16, 32, 64};
 
+int batch_upload_impl(swe_batch *b);
+
+// (no exception crosses the C ABI: a failed host allocation is SWE_ERR_OOM)
 int batch_upload(swe_batch *b) {
+    try {
+        return batch_upload_impl(b);
+    } catch (...) {
+        return SWE_ERR_OOM;
+    }
+}
+
+int batch_upload_impl(swe_batch *b) {
     const int n = (int)b->doms.size();
     std::vector<swe::StageArgs<float>> args(n);
     std::vector<int> start(n + 1, 0), gx(n), rows(n);
