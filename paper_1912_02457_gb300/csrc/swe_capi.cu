@@ -109,7 +109,15 @@ struct swe_domain {
         } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
             ptr = nullptr;
         }
-        if (ptr) owned.push_back(ptr);
+        if (ptr) {
+            try {
+                owned.push_back(ptr);
+            } catch (...) {                      // no exception crosses the C ABI
+                if (release) release(ptr, stream, alloc_ctx);
+                else cudaFree(ptr);
+                ptr = nullptr;
+            }
+        }
         return ptr;
     }
     void dfree(void *ptr) {
@@ -234,7 +242,12 @@ int domain_items(swe_domain *d, int budget, bool alone, const uint2 **dev, int *
                                     d->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) { d->dfree(p); return cuda_fail(e); }
-    d->item_lists.push_back({budget, alone, (int)items.size(), p});
+    try {
+        d->item_lists.push_back({budget, alone, (int)items.size(), p});
+    } catch (...) {
+        d->dfree(p);
+        return SWE_ERR_OOM;
+    }
     *dev = p;
     *n = (int)items.size();
     return SWE_OK;
@@ -598,7 +611,12 @@ int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
     while (h->events.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
-        h->events.push_back(e);
+        try {
+            h->events.push_back(e);
+        } catch (...) {
+            cudaEventDestroy(e);
+            return SWE_ERR_OOM;
+        }
     }
     size_t k = 0;
     for (int s = 0; s < n_steps; s++) {
@@ -918,8 +936,13 @@ int swe_batch_add(swe_batch_handle b, swe_handle d) {
         if (x == d) return SWE_ERR_INVALID_ARG;
     if (step_check(d, 0)) return step_check(d, 0);
     CK(cudaStreamSynchronize(d->stream));      // creation and uploads finished
-    b->doms.push_back(d);
-    b->budget.push_back(b->rows_choice > 0 ? b->rows_choice * swe::kPlanUnit : d->budget);
+    try {
+        b->doms.push_back(d);
+        b->budget.push_back(b->rows_choice > 0 ? b->rows_choice * swe::kPlanUnit : d->budget);
+    } catch (...) {
+        if (b->doms.size() > b->budget.size()) b->doms.pop_back();
+        return SWE_ERR_OOM;
+    }
     return batch_upload(b);
 }
 
