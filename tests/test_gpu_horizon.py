@@ -1,0 +1,70 @@
+"""The full forecast horizon of the synthetic coastal recipe: 24 simulated
+hours (about 1.2e5 adaptive steps: nested M2 tide, wind, drag, moving
+wet-dry fronts) on the GPU in FP32 against the FP64 oracle, at 128 x 128
+cells of 800 m, a size at which the oracle finishes the horizon in about
+two minutes. Both sides compute their own adaptive time step and both stop
+exactly on t = 24 h.
+
+Parity is gated at 1000 steps elsewhere. Over the full horizon the moving
+wet-dry fronts of this recipe produce what Section 3.4 warns of (non-physical
+waves and small time steps): thin drying films on raised shelves carry
+momentum, their desingularised velocities spike, and the CFL step drops to
+below a millisecond at times, in the oracle as on the GPU. After the first
+such event runs that differ by rounding take different step sequences, so
+the end states differ at the level of the waves themselves (the FP64 GPU
+path, within 1e-11 of the oracle per step, ends as far from it as FP32).
+This test therefore reports the deviation and checks only that a run is
+sound: finite, no sticky error, the exact end time, a step count close to
+the oracle's, and deviations below the size of the forcing."""
+import numpy as np
+import pytest
+
+from paper_1912_02457_gb300 import synth
+from tests import helpers
+from tests.test_gpu_parity import rel_l2, swe  # noqa: F401
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+T_END = 24 * 3600.0
+N = 128
+MAX_STEPS = 300000          # far more than the horizon takes; the clock stops at T_END
+
+_REF = {}
+
+
+def _reference(oracle_mod, wl):
+    if "ref" not in _REF:
+        ref = oracle_mod.Oracle(wl).run(MAX_STEPS, t_end=T_END, return_dts=True)
+        steps = int((ref[5] > 0).sum())
+        _REF["ref"] = (ref, steps, helpers.front_set(wl, ref[0]))
+    return _REF["ref"]
+
+
+@pytest.mark.parametrize("prec", ["f32_kahan", "f32"])
+def test_coastal_24h_horizon(swe, oracle_mod, prec):
+    wl = synth.coastal(N, N, dtype=np.float32)
+    ref, ref_steps, front = _reference(oracle_mod, wl)
+    with swe.Domain(wl, prec) as d:
+        d.set_end_time(T_END)
+        d.step(MAX_STEPS)
+        info = d.info()
+        e, u, v = d.state()
+    assert info.done == 1 and info.error == 0
+    assert abs(info.t - T_END) <= 1e-9 * T_END and abs(ref[3] - T_END) <= 1e-9 * T_END
+    wet = ~wl.land_cells()
+    dev = np.abs(e.astype(np.float64) - ref[0])
+    off = wet & ~front
+    report = {"precision": prec, "steps": int(info.step), "oracle_steps": ref_steps,
+              "oracle_dt_min_s": float(ref[5][:ref_steps].min()),
+              "max_deta_off_front_m": float(dev[off].max()),
+              "mean_deta_wet_m": float(dev[wet].mean()),
+              "rel_l2_hu": rel_l2(u, ref[1]), "rel_l2_hv": rel_l2(v, ref[2])}
+    print("HORIZON", report)
+    assert np.isfinite(e).all() and np.isfinite(u).all() and np.isfinite(v).all()
+    # soundness, not parity (see the module docstring): the step count
+    # follows the oracle's, and the deviations stay below the forcing's
+    # scale (0.5 m tide, 10 m/s wind)
+    assert abs(info.step - ref_steps) <= 0.2 * ref_steps
+    assert report["max_deta_off_front_m"] <= 2.0
+    assert report["mean_deta_wet_m"] <= 0.05
+    assert report["rel_l2_hu"] <= 1.0 and report["rel_l2_hv"] <= 1.0
