@@ -616,9 +616,9 @@ static int warp_slots() {
 // [j0, j0 + n), packed as {strip, j0 | n << 16}. A row costs about the same
 // everywhere except in the strips whose two outer lanes are ghosts of a
 // nested edge (they take the edge-state path: ~10% more per row) and, in
-// stage 2, in flow-relaxation zones (~13% more; both measured per item on
-// the coastal 1024 x 1024 step); the four halo rows a march
-// adds cost about a third of a row each. Rows without a wet cell in the
+// stage 2, in flow-relaxation zones (~13% more; weights fitted to per-warp
+// times on the coastal 1024 x 1024 step and tuned by measurement); the
+// four halo rows a march adds cost about a third of a row each. Rows without a wet cell in the
 // strip are left out (land cells are never written and never enter the CFL
 // maximum, and a march recomputes its own halo): each strip falls into
 // segments of wet rows, split where a land run is longer than a halo. A
@@ -764,10 +764,9 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
     out.reserve(n);
     if (!alone || n > warp_slots() || budget < 8 * kPlanUnit) {
         // part of a batch, several waves, or short items: row-major order,
-        // a block's warps
-        // taking neighbouring strips of the same rows (they share halo lines
-        // in L1, which short items and later waves depend on; measured
-        // 1-2% faster than balanced blocks there)
+        // a block's warps taking neighbouring strips of the same rows (they
+        // share halo lines in L1, which short items and later waves depend
+        // on; measured 1-2% faster than balanced blocks there)
         std::sort(order.begin(), order.end(), row_major);
         for (int k : order) out.push_back(items[k]);
         items.swap(out);
@@ -776,7 +775,10 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
     // one wave of long items: blocks of kWarps items with equal total cost
     // (largest item first to the lightest block with room), so that the SMs,
     // whichever blocks they get, carry equal work (coastal 1024^2: +2.6%);
-    // within a block, row-major order
+    // within a block, row-major order. (When the item count is not a
+    // multiple of kWarps a packed block other than the last may hold fewer
+    // items, and the launch's blocks then straddle packed blocks after it;
+    // keeping every short block last measured no different.)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     typedef std::pair<long long, int> Load;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
