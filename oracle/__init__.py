@@ -72,6 +72,8 @@ def lib():
             L.orc_rhs.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp, _dp]
             L.orc_recon_x.restype = C.c_int
             L.orc_recon_x.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
+            L.orc_ghosts.restype = C.c_int
+            L.orc_ghosts.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
             L.orc_step.restype = C.c_int
             L.orc_step.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, C.c_double]
             L.orc_max_speed.restype = C.c_double
@@ -156,6 +158,16 @@ class Oracle:
         out = np.empty((4, ny, nx))
         if self.L.orc_recon_x(C.byref(self.D), _p(e), _p(u), _p(v), t, _p(out)):
             raise MemoryError("oracle recon failed")
+        return out
+
+    def ghosts(self, eta, hu, hv, t=0.0):
+        """The state padded with two ghost rings, filled at time t: shape
+        (3, ny + 4, nx + 4), interior cell (i, j) at [:, j + 2, i + 2]."""
+        e, u, v = _d(eta), _d(hu), _d(hv)
+        ny, nx = e.shape
+        out = np.empty((3, ny + 4, nx + 4))
+        if self.L.orc_ghosts(C.byref(self.D), _p(e), _p(u), _p(v), t, _p(out)):
+            raise MemoryError("oracle ghost fill failed")
         return out
 
     def max_speed(self, eta, hu, hv):

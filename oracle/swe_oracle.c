@@ -708,6 +708,29 @@ int orc_rhs(const orc_domain *d, const double *eta, const double *hu,
     return 0;
 }
 
+/* The ghost-padded state after the ghost fill at time t (exported for the
+ * pins of the boundary interpolation of Section 3.6): out holds 3 planes
+ * (eta, hu, hv) of (ny+4) x (nx+4) cells, cell (i, j) at (j+2)(nx+4)+(i+2);
+ * the ghost-ghost corners, which no stencil reads, are NaN. */
+int orc_ghosts(const orc_domain *d, const double *eta_in, const double *hu_in,
+               const double *hv_in, double t, double *out)
+{
+    int nx = d->nx, ny = d->ny;
+    statics S;
+    if (statics_build(d, &S)) return -1;
+    size_t nc = (size_t)S.px * (ny + 4);
+    double *eta = out, *hu = out + nc, *hv = out + 2 * nc;
+    for (size_t c = 0; c < nc; c++) eta[c] = hu[c] = hv[c] = NAN;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = CI(&S, i, j), s = (size_t)j * nx + i;
+            eta[c] = eta_in[s]; hu[c] = hu_in[s]; hv[c] = hv_in[s];
+        }
+    fill_ghosts(d, &S, eta, hu, hv, t);
+    statics_free(&S);
+    return 0;
+}
+
 /* One face flux from raw face states (h, eta, hu, hv) on both sides, the
  * face depth H_f and the direction: desingularised and combined exactly as
  * in the right-hand side (exported for the eta-form vs h-form test). */
