@@ -51,6 +51,7 @@ class _Domain(C.Structure):
         ("bnd_n", C.c_int), ("bnd_nbx", C.c_int), ("bnd_nby", C.c_int),
         ("bnd_t", C.POINTER(C.c_double)), ("bnd", C.POINTER(C.c_double)),
         ("round_state_f32", C.c_int),
+        ("cfl_faces", C.c_int),
     ]
 
 
@@ -72,6 +73,8 @@ def lib():
             L.orc_rhs.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp, _dp]
             L.orc_recon_x.restype = C.c_int
             L.orc_recon_x.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
+            L.orc_face_speeds.restype = C.c_int
+            L.orc_face_speeds.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
             L.orc_ghosts.restype = C.c_int
             L.orc_ghosts.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
             L.orc_step.restype = C.c_int
@@ -107,7 +110,7 @@ def _p(a):
 class Oracle:
     """The oracle bound to one workload's statics and forcing."""
 
-    def __init__(self, wl, round_state_f32: bool = False):
+    def __init__(self, wl, round_state_f32: bool = False, cfl_faces: bool = False):
         self.wl = wl
         p = wl.params
         nx, ny = wl.nx, wl.ny
@@ -138,6 +141,7 @@ class Oracle:
             D.bnd_n, D.bnd_nbx, D.bnd_nby = len(bt), wl.boundary.nfx, wl.boundary.nfy
             D.bnd_t, D.bnd = _p(bt), _p(bv)
         D.round_state_f32 = int(bool(round_state_f32))
+        D.cfl_faces = int(bool(cfl_faces))
         self.D = D
         self.L = lib()
 
@@ -169,6 +173,15 @@ class Oracle:
         if self.L.orc_ghosts(C.byref(self.D), _p(e), _p(u), _p(v), t, _p(out)):
             raise MemoryError("oracle ghost fill failed")
         return out
+
+    def face_speeds(self, eta, hu, hv, t=0.0):
+        """The largest one-sided local speed max(a+, -a-) over the x-faces
+        and over the y-faces of the reconstruction of a state at time t."""
+        e, u, v = _d(eta), _d(hu), _d(hv)
+        out = np.empty(2)
+        if self.L.orc_face_speeds(C.byref(self.D), _p(e), _p(u), _p(v), t, _p(out)):
+            raise MemoryError("oracle face speeds failed")
+        return float(out[0]), float(out[1])
 
     def max_speed(self, eta, hu, hv):
         e, u, v = _d(eta), _d(hu), _d(hv)

@@ -66,6 +66,14 @@ typedef struct {
      * precision of the paper's GPU code, Section 3.2); arithmetic stays FP64.
      * Used to measure how sensitive a solution is to float32 storage. */
     int round_state_f32;
+    /* Which speeds bound the time step in eq:cfl. 0 (the reading of the
+     * scheme, and what the CUDA path implements): the cell-average
+     * velocities and depths of the current state. 1: the one-sided local
+     * speeds a+, a- of the faces of the current state's reconstruction, the
+     * condition under which Kurganov & Petrova's wet-dry reconstruction keeps
+     * every cell depth non-negative (used by the pins that show why the
+     * cell-average reading does not). */
+    int cfl_faces;
 } orc_domain;
 
 /* ------------------------------------------------------------------------ */
@@ -400,11 +408,13 @@ static face finish_face(raw_face r, double g, double kappa)
  * the pressure is g eta (eta + 2 H_f)/2, i.e. g h^2/2 without the constant
  * g H_f^2/2 that the central-upwind combination returns unchanged.
  * dir 0: x-face (F), dir 1: y-face (G). */
-static void cu_flux(face L, face R, double Hf, double g, int dir, double out[3])
+static void cu_flux(face L, face R, double Hf, double g, int dir, double out[3],
+                    double *speed)
 {
     double unL = dir == 0 ? L.u : L.v, unR = dir == 0 ? R.u : R.v;
     double ap = fmax(fmax(unL + L.c, unR + R.c), 0.0);
     double am = fmin(fmin(unL - L.c, unR - R.c), 0.0);
+    *speed = fmax(ap, -am);
     double pL = 0.5 * g * L.eta * (L.eta + 2.0 * Hf);
     double pR = 0.5 * g * R.eta * (R.eta + 2.0 * Hf);
     if (ap - am == 0.0) {
@@ -593,10 +603,12 @@ static int work_alloc(const statics *S, work *W)
  * Section 3.7, the wind stress of Section 3.5 and the friction rate of
  * the semi-implicit update (reading: S = C_d |u| / |h*|, the quadratic
  * drag -C_d u|u| of eq:swe with a dimensionless coefficient).
- * eta/hu/hv are nx*ny interior arrays; M is 3 planes of nx*ny. */
+ * eta/hu/hv are nx*ny interior arrays; M is 3 planes of nx*ny. *ax, *ay
+ * receive the largest one-sided local speed max(a+, -a-) over the x- and
+ * y-faces that carry a flux. */
 static void rhs(const orc_domain *d, const statics *S, work *W,
                 const double *eta_in, const double *hu_in, const double *hv_in,
-                double t, double *M, double *Sf)
+                double t, double *M, double *Sf, double *ax, double *ay)
 {
     int nx = d->nx, ny = d->ny;
     double *eta = W->eta, *hu = W->hu, *hv = W->hv;
@@ -632,7 +644,8 @@ static void rhs(const orc_domain *d, const statics *S, work *W,
         }
 
     /* fluxes across x-faces i+1/2, i = -1..nx-1 */
-#pragma omp parallel for schedule(static)
+    double sx = 0.0, sy = 0.0;
+#pragma omp parallel for schedule(static) reduction(max: sx)
     for (int j = 0; j < ny; j++)
         for (int i = -1; i < nx; i++) {
             size_t a = CI(S, i, j), b = CI(S, i + 1, j);
@@ -644,9 +657,11 @@ static void rhs(const orc_domain *d, const statics *S, work *W,
             if (!S->land[b]) R = finish_face(xm[b], d->g, d->kappa);
             if (S->land[a]) L = mirror_face(R, 0);
             if (S->land[b]) R = mirror_face(L, 0);
-            cu_flux(L, R, Hf, d->g, 0, out);
+            double sp;
+            cu_flux(L, R, Hf, d->g, 0, out, &sp);
+            sx = fmax(sx, sp);
         }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(max: sy)
     for (int j = -1; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             size_t a = CI(S, i, j), b = CI(S, i, j + 1);
@@ -658,8 +673,12 @@ static void rhs(const orc_domain *d, const statics *S, work *W,
             if (!S->land[b]) R = finish_face(ym[b], d->g, d->kappa);
             if (S->land[a]) L = mirror_face(R, 1);
             if (S->land[b]) R = mirror_face(L, 1);
-            cu_flux(L, R, Hf, d->g, 1, out);
+            double sp;
+            cu_flux(L, R, Hf, d->g, 1, out, &sp);
+            sy = fmax(sy, sp);
         }
+    *ax = sx;
+    *ay = sy;
 
     /* assemble M = -dF/dx - dG/dy + B + C + W, and S */
     size_t np = (size_t)nx * ny;
@@ -702,10 +721,31 @@ int orc_rhs(const orc_domain *d, const double *eta, const double *hu,
     work W;
     if (statics_build(d, &S)) return -1;
     if (work_alloc(&S, &W)) { statics_free(&S); return -1; }
-    rhs(d, &S, &W, eta, hu, hv, t, M, Sf);
+    double ax, ay;
+    rhs(d, &S, &W, eta, hu, hv, t, M, Sf, &ax, &ay);
     work_free(&W);
     statics_free(&S);
     return 0;
+}
+
+/* The largest one-sided local speeds max(a+, -a-) over the x-faces and the
+ * y-faces of one right-hand-side evaluation at time t (out[0], out[1]);
+ * eq:cfl read at the faces bounds the time step by them. */
+int orc_face_speeds(const orc_domain *d, const double *eta, const double *hu,
+                    const double *hv, double t, double *out)
+{
+    size_t np = (size_t)d->nx * d->ny;
+    statics S;
+    work W;
+    if (statics_build(d, &S)) return -1;
+    if (work_alloc(&S, &W)) { statics_free(&S); return -1; }
+    double *M = malloc(3 * np * sizeof(double)), *Sf = malloc(np * sizeof(double));
+    int rc = (!M || !Sf) ? -1 : 0;
+    if (!rc) rhs(d, &S, &W, eta, hu, hv, t, M, Sf, &out[0], &out[1]);
+    free(M); free(Sf);
+    work_free(&W);
+    statics_free(&S);
+    return rc;
 }
 
 /* The ghost-padded state after the ghost fill at time t (exported for the
@@ -739,7 +779,8 @@ void orc_face_flux(const double *left, const double *right, double Hf, double g,
 {
     raw_face a = { left[0], left[1], left[2], left[3] };
     raw_face b = { right[0], right[1], right[2], right[3] };
-    cu_flux(finish_face(a, g, kappa), finish_face(b, g, kappa), Hf, g, dir, out);
+    double speed;
+    cu_flux(finish_face(a, g, kappa), finish_face(b, g, kappa), Hf, g, dir, out, &speed);
 }
 
 /* Face values of the x-reconstruction of every interior cell (eta^E, eta^W,
@@ -833,7 +874,8 @@ static void step(const orc_domain *d, const statics *S, work *W,
 {
     int nx = d->nx, ny = d->ny;
     size_t np = (size_t)nx * ny;
-    rhs(d, S, W, eta, hu, hv, t, M, Sf);
+    double ax, ay;
+    rhs(d, S, W, eta, hu, hv, t, M, Sf, &ax, &ay);
     for (size_t s = 0; s < np; s++) {
         qs[s] = eta[s] + dt * M[s];
         qs[np + s] = (hu[s] + dt * M[np + s]) / (1.0 + dt * Sf[s]);
@@ -841,7 +883,7 @@ static void step(const orc_domain *d, const statics *S, work *W,
     }
     if (d->round_state_f32)
         for (size_t s = 0; s < 3 * np; s++) qs[s] = (double)(float)qs[s];
-    rhs(d, S, W, qs, qs + np, qs + 2 * np, t + dt, M, Sf);
+    rhs(d, S, W, qs, qs + np, qs + 2 * np, t + dt, M, Sf, &ax, &ay);
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             size_t s = (size_t)j * nx + i;
@@ -935,7 +977,17 @@ int orc_run(const orc_domain *d, double *eta, double *hu, double *hv,
     for (int k = 0; k < n && !rc; k++) {
         long s = step0 + k;
         if (dt_fixed > 0.0) *dt = dt_fixed;
-        else if (s % dt_every == 0 || !(*dt > 0.0)) *dt = orc_cfl_dt(d, eta, hu, hv, courant);
+        else if (s % dt_every == 0 || !(*dt > 0.0)) {
+            if (d->cfl_faces) {
+                /* eq:cfl at the faces: the local speeds of the current
+                 * state's reconstruction (one extra evaluation) */
+                double ax, ay;
+                rhs(d, &S, &W, eta, hu, hv, *t, M, Sf, &ax, &ay);
+                *dt = courant * 0.25 / fmax(ax / d->dx, ay / d->dy);
+            } else {
+                *dt = orc_cfl_dt(d, eta, hu, hv, courant);
+            }
+        }
         if (!(*dt > 0.0) || !isfinite(*dt)) { rc = -2; break; }
         /* a forecast horizon: the step that would pass t_end ends on it */
         if (t_end > 0.0) {

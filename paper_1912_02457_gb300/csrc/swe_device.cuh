@@ -244,8 +244,9 @@ __device__ __forceinline__ void axis_pos_f(int k, int n, int nb, int &k0, int &k
 }
 
 // Wind stress at cell (i, j) at the stage time (Section 3.5): uniform
-// frames use the stress the clock kernel computed in FP64; gridded frames
-// are sampled bilinearly at the cell centre and lerped in time here.
+// frames use the stress the clock kernel computed; gridded frames are
+// sampled bilinearly at the cell centre and lerped in time here, in the
+// domain's precision.
 // Bounds checks of the debug builds (-DSWE_DEBUG_BOUNDS): SWE_CHECK(a, off,
 // n) is true when 0 <= off < n; otherwise it records SWE_ERR_BOUNDS (with
 // the source line in err_cell) and the caller skips the access. In product
@@ -275,25 +276,36 @@ __device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int
         return;
     }
     const ForcingDev &F = a.wind;
+    // sampling positions and weights in the domain's precision (an FP64
+    // domain interpolates in FP64, like its nesting frames)
     int x0, x1, y0, y1;
-    float wx, wy;
-    axis_pos_f(i, a.nx, F.n1, x0, x1, wx);
-    axis_pos_f(j, a.ny, F.n2, y0, y1, wy);
+    T wx, wy;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        double px, py;
+        axis_pos(i, a.nx, F.n1, x0, x1, px);
+        axis_pos(j, a.ny, F.n2, y0, y1, py);
+        wx = T(px); wy = T(py);
+    } else {
+        float px, py;
+        axis_pos_f(i, a.nx, F.n1, x0, x1, px);
+        axis_pos_f(j, a.ny, F.n2, y0, y1, py);
+        wx = T(px); wy = T(py);
+    }
     int fk = a.ctl->wk[stage];
-    float s = (float)a.ctl->ws[stage];
+    T s = T(a.ctl->ws[stage]);
     long long fs = 2LL * F.n1 * F.n2;
     const long long oa = fk * fs, ob = F.n > 1 ? oa + fs : oa;
-    auto A = [&](long long o) { return SWE_CHECK(a, oa + o, a.n_wind) ? F.frames[oa + o] : 0.f; };
-    auto B = [&](long long o) { return SWE_CHECK(a, ob + o, a.n_wind) ? F.frames[ob + o] : 0.f; };
-    float W[2];
+    auto A = [&](long long o) { return T(SWE_CHECK(a, oa + o, a.n_wind) ? F.frames[oa + o] : 0.f); };
+    auto B = [&](long long o) { return T(SWE_CHECK(a, ob + o, a.n_wind) ? F.frames[ob + o] : 0.f); };
+    T W[2];
     for (int c = 0; c < 2; c++) {
-        float a0 = (1.f - wx) * A((y0 * F.n1 + x0) * 2 + c) + wx * A((y0 * F.n1 + x1) * 2 + c);
-        float a1 = (1.f - wx) * A((y1 * F.n1 + x0) * 2 + c) + wx * A((y1 * F.n1 + x1) * 2 + c);
-        float b0 = (1.f - wx) * B((y0 * F.n1 + x0) * 2 + c) + wx * B((y0 * F.n1 + x1) * 2 + c);
-        float b1 = (1.f - wx) * B((y1 * F.n1 + x0) * 2 + c) + wx * B((y1 * F.n1 + x1) * 2 + c);
-        W[c] = (1.f - s) * ((1.f - wy) * a0 + wy * a1) + s * ((1.f - wy) * b0 + wy * b1);
+        T a0 = (T(1) - wx) * A((y0 * F.n1 + x0) * 2 + c) + wx * A((y0 * F.n1 + x1) * 2 + c);
+        T a1 = (T(1) - wx) * A((y1 * F.n1 + x0) * 2 + c) + wx * A((y1 * F.n1 + x1) * 2 + c);
+        T b0 = (T(1) - wx) * B((y0 * F.n1 + x0) * 2 + c) + wx * B((y0 * F.n1 + x1) * 2 + c);
+        T b1 = (T(1) - wx) * B((y1 * F.n1 + x0) * 2 + c) + wx * B((y1 * F.n1 + x1) * 2 + c);
+        W[c] = (T(1) - s) * ((T(1) - wy) * a0 + wy * a1) + s * ((T(1) - wy) * b0 + wy * b1);
     }
-    wind_stress<T>(T(W[0]), T(W[1]), rho_ratio, tx, ty);
+    wind_stress<T>(W[0], W[1], rho_ratio, tx, ty);
 }
 
 // CFL wave speed of one cell, eq:cfl: max((|u| + sqrt(g hbar+))/dx,

@@ -189,3 +189,22 @@ def periodic_rough(nx, ny, seed=0, land=False, periodic=(True, True), dtype=np.f
                         eta=z0.copy(), hu=z0.copy(), hv=z0.copy(), H=Hc, f=f, theta=th,
                         bc=bc, params=synth.Params())
     return wl.astype(dtype)
+
+
+def gridded_wind(nfx, nfy, hours=3, seed=0, speed=10.0):
+    """Hourly wind frames on a coarse nfx x nfy grid (grid axes, m/s): a
+    smooth field that turns and strengthens across the grid and changes
+    from hour to hour, speeds of roughly 4-16 m/s (both branches of the
+    Large & Pond drag law)."""
+    rng = np.random.default_rng(seed)
+    n = hours + 1
+    X = (np.arange(nfx) + 0.5) / nfx
+    Y = (np.arange(nfy) + 0.5) / nfy
+    fr = np.zeros((n, nfy, nfx, 2), dtype=np.float32)
+    for q in range(n):
+        a = rng.uniform(-0.6, 0.6)
+        ang = a + 1.2 * X[None, :] - 0.8 * Y[:, None]
+        sp = speed * (1.0 + 0.5 * np.sin(2.0 * np.pi * (X[None, :] + 0.7 * Y[:, None] + 0.3 * q)))
+        fr[q, :, :, 0] = sp * np.cos(ang)
+        fr[q, :, :, 1] = sp * np.sin(ang)
+    return synth.Forcing(times=3600.0 * np.arange(n, dtype=np.float64), frames=fr, nfx=nfx, nfy=nfy)

@@ -127,6 +127,35 @@ def test_small_coastal_f32(swe, oracle_mod, prec):
     assert abs(info.t - ref[3]) <= 1e-6 * ref[3]
 
 
+def _coastal_gridded_wind(dtype, member, nfx=7, nfy=5):
+    """The small coastal domain under a wind that varies across a coarse
+    7 x 5 grid and from hour to hour (trilinear interpolation, Section 3.5),
+    with the recipe's tide frames at half resolution along each edge."""
+    wl = _small_coastal(dtype=dtype, member=member)
+    wl.wind = helpers.gridded_wind(nfx, nfy, hours=3, seed=member)
+    return wl
+
+
+def test_gridded_wind_f64(swe, oracle_mod):
+    wl = _coastal_gridded_wind(np.float64, member=7)
+    ref = oracle_mod.Oracle(wl).run(300)
+    st, info = gpu_run(swe, wl, 300, "f64")
+    for a, b in zip(st, ref[:3]):
+        assert helpers.rel(a, b) <= 1e-11
+    assert abs(info.t - ref[3]) <= 1e-11 * ref[3]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_gridded_wind_f32(swe, oracle_mod, prec):
+    wl = _coastal_gridded_wind(np.float32, member=9)
+    if "gridded" not in _REF_CACHE:
+        _REF_CACHE["gridded"] = front_references(oracle_mod, wl, 1000)
+    ref, front = _REF_CACHE["gridded"]
+    st, info = gpu_run(swe, wl, 1000, prec)
+    assert_f32_parity_fronts(st, wl, ref, front)
+    assert abs(info.t - ref[3]) <= 1e-6 * ref[3]
+
+
 @pytest.mark.parametrize("shape", [(37, 23), (33, 9), (1, 17), (17, 1), (2, 2), (65, 130)])
 def test_ragged_shapes_f64(swe, oracle_mod, shape):
     nx, ny = shape
