@@ -215,13 +215,17 @@ def still_boundary(nx: int, ny: int, eta: float = 0.0,
 
 def tide_boundary(nx: int, ny: int, dx: float, dy: float, H_edge: dict,
                   amp: float = 0.5, hours: int = 25, nb_div: int = 2,
-                  phase0: float = 0.0, g: float = 9.81) -> Forcing:
+                  phase0: float = 0.0, g: float = 9.81,
+                  eta_floor: Optional[dict] = None) -> Forcing:
     """Hourly M2 frames: eta = amp*sin(2 pi t / T + phi), phi = 2 pi s / L.
 
     s is the along-boundary coordinate of the ghost-cell centre (x + y, m),
     L = T sqrt(g Hbar_edge) the tidal wavelength over the edge's mean depth;
     hu = hv = 0 in the frames. Frames are stored at 1/nb_div of the domain's
-    resolution along each edge (a coarser parent model)."""
+    resolution along each edge (a coarser parent model). ``eta_floor`` maps
+    an edge to the lowest level each of its samples may take (an external
+    model keeps dry land dry: its level never lies below the bed it
+    covers)."""
     nbx, nby = max(nx // nb_div, 1), max(ny // nb_div, 1)
     times = 3600.0 * np.arange(hours + 1, dtype=np.float64)
     fr = np.zeros((len(times), 12 * (nbx + nby)), dtype=np.float32)
@@ -242,9 +246,42 @@ def tide_boundary(nx: int, ny: int, dx: float, dy: float, H_edge: dict,
             else:
                 xs, ys = (nx + r + 0.5) * dx, k * ny * dy
             phi = 2 * np.pi * (xs + ys) / L + phase0
-            blk[:, r, 0, :] = (amp * np.sin(2 * np.pi * times[:, None] / M2_PERIOD
-                                            + phi[None, :])).astype(np.float32)
+            eta = amp * np.sin(2 * np.pi * times[:, None] / M2_PERIOD + phi[None, :])
+            if eta_floor is not None and e in eta_floor:
+                eta = np.maximum(eta, eta_floor[e][None, :])
+            blk[:, r, 0, :] = eta.astype(np.float32)
     return Forcing(times=times, frames=fr, nfx=nbx, nfy=nby)
+
+
+def edge_sample_floor(Hbar: np.ndarray, land: np.ndarray, zone: int, nb_div: int = 2) -> dict:
+    """The lowest external level each boundary sample of the S, N and W
+    edges may take so that no cell it reaches lies below the bed. A cell
+    filled from an edge (the ghost rings copy the statics of the first two
+    rows) or relaxed toward it (the zone of ``zone`` rows) takes the edge's
+    level interpolated linearly between the two nearest samples at the
+    cell's position along the edge. Each sample is raised to at least -Hbar
+    of every wet zone cell whose interpolation uses it, so every
+    interpolated level covers the bed (a convex combination of levels that
+    do). Plain data preparation, no step of the scheme."""
+    out = {}
+    for e in ("S", "N", "W"):
+        if e == "S":
+            hb, lm = Hbar[:zone, :].T, land[:zone, :].T
+        elif e == "N":
+            hb, lm = Hbar[::-1][:zone, :].T, land[::-1][:zone, :].T
+        else:
+            hb, lm = Hbar[:, :zone], land[:, :zone]
+        need = np.where(lm, -np.inf, -hb).max(axis=1)   # per cell along the edge
+        n = need.shape[0]
+        nb = max(n // nb_div, 1)
+        p = np.clip((np.arange(n) + 0.5) * nb / n - 0.5, 0.0, nb - 1)
+        k0 = np.floor(p).astype(int)
+        k1 = np.minimum(k0 + 1, nb - 1)
+        floor = np.full(nb, -np.inf)
+        np.maximum.at(floor, k0, need)
+        np.maximum.at(floor, k1, need)
+        out[e] = floor
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -284,6 +321,8 @@ def coastal(nx: int = 1024, ny: int = 1024, seed_config: int = 2,
       north angle linear in x over 0-0.3 rad;
     * quadratic drag Cd = 0.0025; uniform 10 m/s wind along +x;
     * nested S, N, W edges with hourly M2 tide frames (0.5 m), east wall;
+      the frames' level is kept at or above the bed of every cell it fills
+      or relaxes (raised shelves reaching the edge stay dry);
     * initial state at rest: eta = max(0, -Hbar) on water, 0 on land.
     """
     rng = rng_for(seed_config, member)
@@ -313,8 +352,9 @@ def coastal(nx: int = 1024, ny: int = 1024, seed_config: int = 2,
     for e, row in (("S", Hbar[0]), ("N", Hbar[-1]), ("W", Hbar[:, 0])):
         wet = row[row > 0]
         H_edge[e] = float(wet.mean()) if wet.size else 100.0
+    floor = edge_sample_floor(Hbar, wl_land, Params().frs_width)
     bnd = tide_boundary(nx, ny, dx, dy, H_edge, amp=0.5, hours=hours + 1,
-                        phase0=tide_phase)
+                        phase0=tide_phase, eta_floor=floor)
     wr = math.radians(wind_dir_deg)
     wind = uniform_wind(wind_speed * math.cos(wr), wind_speed * math.sin(wr))
     return Workload(name=f"coastal{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dy,
