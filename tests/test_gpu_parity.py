@@ -63,22 +63,44 @@ def front_references(oracle_mod, wl, n):
     return ref, front
 
 
-def assert_f32_parity_fronts(gpu, wl, ref, front):
-    """FP32 parity on a domain with moving wet-dry fronts: max |d eta| <=
-    1e-4 m on every wet cell outside the front set (the coastal band within
-    three cells of a dry cell: ~10% of the wet cells at 1024^2, at most 25%
-    on small domains); inside it |d eta| <= 1 cm; the mean |d eta| over all
-    wet cells below 1e-5 m and the relative L2 error of hu and hv below 1e-4."""
+def front_report(gpu, wl, ref, front):
+    """Where the front set lies and how far the float32 run is from the
+    oracle inside and outside it (printed beside every front-aware check)."""
     e, u, v = gpu
     wet = ~wl.land_cells()
+    off = wet & ~front
     dev = np.abs(e.astype(np.float64) - ref[0])
-    assert front.sum() <= 0.25 * wet.sum(), (front.sum(), wet.sum())
-    assert dev[wet & ~front].max() <= 1e-4, dev[wet & ~front].max()
-    if front.any():
-        assert dev[front].max() <= 1e-2, dev[front].max()
-    assert dev[wet].mean() <= 1e-5, dev[wet].mean()
-    assert rel_l2(u, ref[1]) <= 1e-4
-    assert rel_l2(v, ref[2]) <= 1e-4
+    rows, cols = np.nonzero(front)
+    rep = {"front_cells": int(front.sum()), "wet_cells": int(wet.sum()),
+           "front_share": round(float(front.sum() / max(wet.sum(), 1)), 4),
+           "front_rows": [int(rows.min()), int(rows.max())] if rows.size else None,
+           "front_cols": [int(cols.min()), int(cols.max())] if cols.size else None,
+           "max_deta_off_front": float(dev[off].max()),
+           "max_deta_front": float(dev[front].max()) if front.any() else 0.0,
+           "mean_deta_wet": float(dev[wet].mean()),
+           "rel_l2_hu_off_front": rel_l2(u[off], ref[1][off]),
+           "rel_l2_hv_off_front": rel_l2(v[off], ref[2][off]),
+           "rel_l2_hu": rel_l2(u, ref[1]), "rel_l2_hv": rel_l2(v, ref[2])}
+    print("FRONT_BAND", rep)
+    return rep
+
+
+def assert_f32_parity_fronts(gpu, wl, ref, front):
+    """FP32 parity on a domain with moving wet-dry fronts. Outside the front
+    set: max |d eta| <= 1e-4 m and relative L2 errors of hu and hv <= 1e-4.
+    Inside it (the coastal band within three cells of a dry cell: ~10% of
+    the wet cells at 1024^2, at most 25% on small domains): |d eta| <= 1 cm.
+    Over all wet cells: mean |d eta| <= 1e-5 m and the relative L2 errors of
+    hu and hv <= 1e-3. The FP64 oracle itself, with its state stored in
+    float32, moves by as much on the fronts (test_oracle_fronts.py); the
+    band's size, place and errors are printed."""
+    rep = front_report(gpu, wl, ref, front)
+    assert rep["front_cells"] <= 0.25 * rep["wet_cells"], rep
+    assert rep["max_deta_off_front"] <= 1e-4, rep
+    assert rep["max_deta_front"] <= 1e-2, rep
+    assert rep["mean_deta_wet"] <= 1e-5, rep
+    assert rep["rel_l2_hu_off_front"] <= 1e-4 and rep["rel_l2_hv_off_front"] <= 1e-4, rep
+    assert rep["rel_l2_hu"] <= 1e-3 and rep["rel_l2_hv"] <= 1e-3, rep
 
 
 def test_gaussian_f64_1000_steps(swe, oracle_mod):

@@ -4,8 +4,9 @@ Whether a dry cell wets on a given step is a threshold decision (the face
 depths of eq:hE and the re-sloping of eq:KxE_adjust). Perturbing the FP64
 oracle at float32 level (its inputs moved by one ulp, or its state stored in
 float32 after every stage) moves its solution by more than 1e-4 m on front
-cells after 1000 steps and by far less everywhere else. This is why the GPU
-parity tests hold float32 results to 1e-4 m off the fronts and bound them
+cells after 1000 steps and by far less everywhere else; the momentum of the
+thin films there moves as much. This is why the GPU parity tests hold
+float32 results to 1e-4 (level and momentum) off the fronts and bound them
 separately on the fronts."""
 import numpy as np
 
@@ -26,3 +27,13 @@ def test_front_sensitivity_is_confined_to_fronts(oracle_mod):
     assert d_ulp[wet & ~front].max() < 1e-6
     assert d_f32[wet & ~front].max() < 5e-5
     assert max(d_ulp[front].max(), d_f32[front].max()) > 1e-4
+    # the momentum of front cells (thin films) moves as much: float32
+    # storage alone shifts the relative L2 error of the whole domain past
+    # 1e-4, while off the fronts it stays well inside it
+    off = wet & ~front
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+    assert max(rel(f32[1], ref[1]), rel(f32[2], ref[2])) > 1e-4
+    assert max(rel(f32[1][off], ref[1][off]), rel(f32[2][off], ref[2][off])) < 5e-5
