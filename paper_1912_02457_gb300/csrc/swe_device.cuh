@@ -158,15 +158,12 @@ __device__ __forceinline__ void cu_flux(const Face<T> &L, const Face<T> &R, T Hf
     T den = ap - am;
     T pL = T(0.5) * g * L.eta * (L.eta + T(2) * Hf);
     T pR = T(0.5) * g * R.eta * (R.eta + T(2) * Hf);
-    if (den == T(0)) {
-        // two dry faces at rest: the h-form flux is zero, i.e. the eta-form
-        // normal momentum flux is the dry pressure -g H_f^2/2 (= pL = pR)
-        out[0] = T(0);
-        out[1] = DIR == 0 ? pL : T(0);
-        out[2] = DIR == 0 ? T(0) : pL;
-        return;
-    }
-    T rd = T(1) / den;
+    // two dry faces at rest (a+ = a- = 0): the h-form flux is zero, i.e. the
+    // eta-form normal momentum flux is the dry pressure -g H_f^2/2 (= pL = pR).
+    // Selected at the end rather than branched to, so the flux has no
+    // divergent path.
+    const bool rest = den == T(0);
+    T rd = T(1) / (rest ? T(1) : den);
     T FL0, FL1, FL2, FR0, FR1, FR2;
     if (DIR == 0) {
         FL0 = L.hu; FL1 = L.hu * L.u + pL; FL2 = L.hu * L.v;
@@ -176,9 +173,12 @@ __device__ __forceinline__ void cu_flux(const Face<T> &L, const Face<T> &R, T Hf
         FR0 = R.hv; FR1 = R.hv * R.u; FR2 = R.hv * R.v + pR;
     }
     T apam = ap * am;
-    out[0] = (ap * FL0 - am * FR0 + apam * (R.eta - L.eta)) * rd;
-    out[1] = (ap * FL1 - am * FR1 + apam * (R.hu - L.hu)) * rd;
-    out[2] = (ap * FL2 - am * FR2 + apam * (R.hv - L.hv)) * rd;
+    const T o0 = (ap * FL0 - am * FR0 + apam * (R.eta - L.eta)) * rd;
+    const T o1 = (ap * FL1 - am * FR1 + apam * (R.hu - L.hu)) * rd;
+    const T o2 = (ap * FL2 - am * FR2 + apam * (R.hv - L.hv)) * rd;
+    out[0] = rest ? T(0) : o0;
+    out[1] = rest ? (DIR == 0 ? pL : T(0)) : o1;
+    out[2] = rest ? (DIR == 0 ? T(0) : pL) : o2;
 }
 
 // Large & Pond wind stress (Section 3.5).

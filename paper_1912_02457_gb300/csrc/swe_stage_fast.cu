@@ -127,12 +127,35 @@ __device__ void edge_fill(const StageArgs<float> &a, int slot, int stage, int id
 // is.
 template <int STAGE>
 struct RawCell {
-    float c00, c10, c01, c11, f, th, q0, q1, q2, d0, d1, d2;
+    float c00, c10, c01, c11, f, q0, q1, q2, d0, d1, d2;
 };
 
 template <int STAGE>
 __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, int i, int r,
-                                           RawCell<STAGE> &w) {
+                                           bool interior, RawCell<STAGE> &w,
+                                           const RawCell<STAGE> *below = nullptr) {
+    if (interior) {
+        // the warp's whole item and its halo lie inside the domain: plain
+        // loads of the cell's corners, Coriolis parameter and state; the
+        // lower corners are the upper corners of the cell below when the
+        // march has it
+        const int cp = (int)a.cpitch;
+        const int h0 = r * cp + i;
+        const int s = r * (int)a.pitch + i;
+        if (!(SWE_CHECK(a, h0, a.n_corner) && SWE_CHECK(a, h0 + cp + 1, a.n_corner) &&
+              SWE_CHECK(a, s, a.n_plane))) {
+            w.c00 = w.c10 = w.c01 = w.c11 = kLand;
+            return;
+        }
+        const float *H = a.H + h0;
+        if (below) { w.c00 = below->c01; w.c10 = below->c11; }
+        else       { w.c00 = __ldg(H); w.c10 = __ldg(H + 1); }
+        w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
+        w.f = a.f ? __ldg(a.f + s) : a.f_const;
+        w.q0 = __ldg(a.q[par][0] + s); w.q1 = __ldg(a.q[par][1] + s); w.q2 = __ldg(a.q[par][2] + s);
+        if (STAGE == 2) { w.d0 = __ldg(a.d1[0] + s); w.d1 = __ldg(a.d1[1] + s); w.d2 = __ldg(a.d1[2] + s); }
+        return;
+    }
     const int nx = a.nx, ny = a.ny;
     const bool ox = (unsigned)i >= (unsigned)nx, oy = (unsigned)r >= (unsigned)ny;
     int si = i, sj = r, e = -1, ring = 0;
@@ -171,7 +194,6 @@ __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, i
     const float *H = a.H + h0;
     w.c00 = __ldg(H); w.c10 = __ldg(H + 1); w.c01 = __ldg(H + cp); w.c11 = __ldg(H + cp + 1);
     w.f = a.f ? __ldg(a.f + s) : a.f_const;
-    w.th = a.th ? __ldg(a.th + s) : a.th_const;
     const float *p0 = a.q[par][0] + s, *p1 = a.q[par][1] + s, *p2 = a.q[par][2] + s;
     if (e >= 0) {
         p0 = a.edge + pe;
@@ -191,7 +213,7 @@ __device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int i, in
     c.land = (w.c00 == kLand) | (w.c10 == kLand) | (w.c01 == kLand) | (w.c11 == kLand);
     if (c.land) {
         c.eta = c.hu = c.hv = c.Hbar = c.HE = c.HW = c.HN = c.HS = 0.f;
-        c.f = c.ct = c.st = c.hbar = c.hs = c.u = c.v = c.fvx = c.fuy = 0.f;
+        c.f = c.hbar = c.hs = c.u = c.v = c.fvx = c.fuy = 0.f;
         return;
     }
     c.Hbar = 0.25f * (w.c00 + w.c10 + w.c01 + w.c11);
@@ -204,10 +226,20 @@ __device__ __forceinline__ void decode_cell(const StageArgs<float> &a, int i, in
     c.HE = swap_x ? HW : HE; c.HW = swap_x ? HE : HW;
     c.HN = swap_y ? HS : HN; c.HS = swap_y ? HN : HS;
     c.f = w.f;
-    __sincosf(w.th, &c.st, &c.ct);
     c.eta = w.q0; c.hu = w.q1; c.hv = w.q2;
     if (STAGE == 2) { c.eta += w.d0; c.hu += w.d1; c.hv += w.d2; }
-    make_prim(c, a.kappa, a.half_inv_kappa);
+    // primitives (Sections 3.1, 3.2, 3.7): hbar, h*, u = hu/h*, v = hv/h*.
+    // The north-vector projection of Section 3.7 enters the reconstruction
+    // as f x.[v^n, -u^e] and -f y.[v^n, -u^e]; rotating (u, v) into the
+    // local east/north frame and back is the identity for every angle, so
+    // these are f v and f u and the north angle is not read.
+    c.hbar = c.eta + c.Hbar;
+    c.hs = desing(c.hbar, a.kappa, a.half_inv_kappa);
+    const float rcp = 1.f / c.hs;
+    c.u = c.hu * rcp;
+    c.v = c.hv * rcp;
+    c.fvx = c.f * c.v;
+    c.fuy = c.f * c.u;
 }
 
 // The part of a cell the y-reconstruction of later rows needs.
@@ -339,11 +371,10 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
         acc0[0] = -(Fe[0] - Fw[0]) * a.inv_dx;
         acc0[1] = -(Fe[1] - Fw[1]) * a.inv_dx + g * 0.5f * (etaE + etaW) * (c.HE - c.HW) * a.inv_dx;
         acc0[2] = -(Fe[2] - Fw[2]) * a.inv_dx;
-        // Coriolis with the north vector (Section 3.7) and wind stress
-        float hue = c.ct * c.hu - c.st * c.hv;
-        float hvn = c.st * c.hu + c.ct * c.hv;
-        acc0[1] += c.f * (c.ct * hvn - c.st * hue);
-        acc0[2] += c.f * (-c.st * hvn - c.ct * hue);
+        // Coriolis (Section 3.7: f x.[hv^n, -hu^e] = f hv and
+        // f y.[hv^n, -hu^e] = -f hu for every north angle) and wind stress
+        acc0[1] += c.f * c.hv;
+        acc0[2] -= c.f * c.hu;
         if (k.wind_on) {
             if (k.wind_uni) {
                 acc0[1] += k.taux;
@@ -522,10 +553,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     if (strip_live) {
         const int i = k.i, j0 = k.j0, j1 = k.j1, par = k.par;
         RawCell<STAGE> cur, nxt;
-        fetch_cell<STAGE>(a, par, i, j0 - 2, cur);
+        // warp-uniform: every cell the march loads is an interior cell
+        const bool interior = strip * kStrip - 2 >= 0 && strip * kStrip + 29 < a.nx && j0 - 2 >= 0 &&
+                              j1 + 1 < a.ny;
+        fetch_cell<STAGE>(a, par, i, j0 - 2, interior, cur);
         SWE_UNROLL_PRAGMA(SWE_UNROLL)
         for (int r = j0 - 2; r <= j1 + 1; r++) {
-            if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, nxt);
+            if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, interior, nxt, &cur);
             Cell<float> c;
             decode_cell<STAGE>(a, i, r, cur, c);
             // which parts this row runs (warp-uniform): see march_row
