@@ -76,9 +76,13 @@ typedef struct {
     double rho_air;         /* 1.225 (Section 3.5) */
     double rho_water;       /* 1025 */
     double t0;              /* initial simulated time, s */
-    int kernel;             /* 0: fastest kernels for the precision (FP32:
-                               sliding-window stage kernels); 1: the
-                               one-thread-per-cell reference kernels */
+    int kernel;             /* 0 (use this): the kernels of the precision,
+                               the sliding-window stage kernels for FP32
+                               domains and the one-thread-per-cell kernels
+                               for FP64 ones; 1: test instrument only, FP32
+                               domains on the one-thread-per-cell kernels
+                               (slower, not batchable), kept so that tests
+                               can cross-check the two FP32 kernel sets */
 } swe_params;
 
 /* Domain description. Arrays are read once by swe_create_domain and
@@ -278,7 +282,10 @@ int swe_batch_destroy(swe_batch_handle b);
  * any stream capture. Every call writes the partials it reads, so nothing
  * carries over between calls, but all calls share the one array: calls
  * that overlap on the GPU (other streams, other host threads) race, so
- * order them on one stream. */
+ * order them on one stream. Devices with an ordinal of 64 or more are not
+ * supported (SWE_ERR_UNSUPPORTED); SWE_ERR_CUDA reports a failed address
+ * lookup or a failed launch of this call (an error left pending by earlier
+ * calls is neither reported nor cleared). */
 #define SWE_NOALLOC_MAX_ROWS 16384
 int swe_diagnostics_noalloc(const float *eta, const float *hu, const float *hv, const float *H,
                             int nx, int ny, long long pitch, long long cpitch, double dx,

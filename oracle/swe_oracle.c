@@ -976,6 +976,8 @@ int orc_run(const orc_domain *d, double *eta, double *hu, double *hv,
     int rc = (!M || !Sf || !qs) ? -1 : 0;
     for (int k = 0; k < n && !rc; k++) {
         long s = step0 + k;
+        /* past the forecast horizon every further step is a no-op */
+        if (t_end > 0.0 && *t >= t_end * (1.0 - 1e-14)) { if (dts) dts[k] = 0.0; continue; }
         if (dt_fixed > 0.0) *dt = dt_fixed;
         else if (s % dt_every == 0 || !(*dt > 0.0)) {
             if (d->cfl_faces) {
@@ -990,10 +992,7 @@ int orc_run(const orc_domain *d, double *eta, double *hu, double *hv,
         }
         if (!(*dt > 0.0) || !isfinite(*dt)) { rc = -2; break; }
         /* a forecast horizon: the step that would pass t_end ends on it */
-        if (t_end > 0.0) {
-            if (*t >= t_end * (1.0 - 1e-14)) { if (dts) dts[k] = 0.0; continue; }
-            if (*t + *dt > t_end) *dt = t_end - *t;
-        }
+        if (t_end > 0.0 && *t + *dt > t_end) *dt = t_end - *t;
         step(d, &S, &W, eta, hu, hv, *t, *dt, M, Sf, qs);
         if (dts) dts[k] = *dt;
         *t += *dt;

@@ -79,7 +79,8 @@ __global__ void rows_total_kernel(const double *partials, int ny, double area, d
 int scratch_on_current_device(double **ptr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SWE_ERR_CUDA;
+    if (e != cudaSuccess) return SWE_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return SWE_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_partials_addr[dev]) {
         void *p = nullptr;
@@ -106,9 +107,16 @@ int swe_diagnostics_noalloc(const float *eta, const float *hu, const float *hv, 
     int rc = scratch_on_current_device(&partials);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    row_sums_kernel<<<ny, 256, 0, st>>>(eta, hu, hv, H, nx, ny, pitch, cpitch, g, kappa, partials);
-    rows_total_kernel<<<1, 32, 0, st>>>(partials, ny, dx * dy, out);
-    return cudaGetLastError() == cudaSuccess ? SWE_OK : SWE_ERR_CUDA;
+    // launched through cudaLaunchKernel, whose status is that of this launch
+    // alone (an error the caller left pending is neither reported nor cleared)
+    double area = dx * dy;
+    void *row_args[] = {&eta, &hu, &hv, &H, &nx, &ny, &pitch, &cpitch, &g, &kappa, &partials};
+    if (cudaLaunchKernel((const void *)row_sums_kernel, dim3(ny), dim3(256), row_args, 0, st) != cudaSuccess)
+        return SWE_ERR_CUDA;
+    void *total_args[] = {&partials, &ny, &area, &out};
+    if (cudaLaunchKernel((const void *)rows_total_kernel, dim3(1), dim3(32), total_args, 0, st) != cudaSuccess)
+        return SWE_ERR_CUDA;
+    return SWE_OK;
 }
 
 }  // extern "C"

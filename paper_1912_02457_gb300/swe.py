@@ -237,6 +237,12 @@ def use_torch_allocator():
     _torch_alloc_refs = refs
 
 
+def use_default_allocator():
+    """Domains created from now on allocate with cudaMalloc again (domains
+    created under another allocator keep returning their buffers to it)."""
+    _check(load().swe_set_allocator(None, None, None), "swe_set_allocator")
+
+
 class Domain:
     """One simulated domain held by libswe.
 

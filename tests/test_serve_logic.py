@@ -27,23 +27,30 @@ class FakeBackend:
         self.ids = itertools.count()
         self.max_live = 0
 
-    def open(self, wl, precision, horizon):
+    def create(self, wl, precision, horizon):
         if wl == "boom":
             raise RuntimeError("allocation failed")
         h = next(self.ids)
-        self.live[h] = [0, int(horizon)]
+        self.live[h] = [0, int(horizon), False]
         self.max_live = max(self.max_live, len(self.live))
         return h
+
+    def join(self, h):
+        self.live[h][2] = True
 
     def step(self, n):
         self.clock.t += n * self.dt_wall
         for v in self.live.values():
-            v[0] = min(v[0] + n, v[1])
+            if v[2]:
+                v[0] = min(v[0] + n, v[1])
 
     def poll(self, handles):
         return [self.live[h][0] >= self.live[h][1] for h in handles]
 
-    def close(self, h, download=True):
+    def leave(self, h):
+        self.live[h][2] = False
+
+    def result(self, h, download=True):
         steps = self.live.pop(h)[0]
         return ("state", h) if download else None, steps
 
@@ -70,6 +77,8 @@ def test_tiny_budget_is_respected_and_all_are_served():
     assert adm == sorted(adm)
     st = serve.ForecastServer.stats(reqs, wall=clock.t)
     assert st["served"] == 7 and st["p99_latency_s"] >= st["p50_latency_s"] > 0
+    # later arrivals were admitted while earlier ones were on the device
+    assert srv.overlapped > 0
 
 
 def test_faults_do_not_stop_the_server():

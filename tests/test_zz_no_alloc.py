@@ -50,6 +50,55 @@ def test_noalloc_matches_diagnostics_twice(swe):
             assert _close(got[0], want[0]) and _close(got[1], want[1]), (got, want)
 
 
+def _device_planes(swe, d, nx, ny):
+    import torch
+    planes = [torch.empty((ny, nx), dtype=torch.float32, device="cuda") for _ in range(3)]
+    for field, t in zip((swe.ETA, swe.HU, swe.HV), planes):
+        d.read_device(field, t.data_ptr())
+    torch.cuda.synchronize()
+    return planes
+
+
+def test_noalloc_and_domain_diagnostics_match_oracle(swe, oracle_mod):
+    """An FP32 coastal state: the domain's own diagnostics (which use the
+    domain's float32 g and kappa) against the oracle given the same two
+    values, and the allocation-free call with the exact g and kappa against
+    the oracle as configured by the workload, both to 1e-12. Free device
+    memory does not move across a call (after the first, which loads the
+    library's module)."""
+    import torch
+    wl = synth.coastal(300, 220, seed_config=96, member=1, dtype=np.float32)
+    nx, ny = wl.nx, wl.ny
+    H = torch.from_numpy(np.ascontiguousarray(wl.H)).cuda()
+    with swe.Domain(wl, "f32") as d:
+        d.step(9)
+        state = d.state()
+        dom = d.diagnostics()
+        planes = _device_planes(swe, d, nx, ny)
+    w32 = wl.copy()
+    w32.params.g = float(np.float32(wl.params.g))
+    w32.params.kappa = float(np.float32(wl.params.kappa))
+    om32 = oracle_mod.Oracle(w32).diagnostics(*state)
+    assert _close(dom[0], om32[0]) and _close(dom[1], om32[1]), (dom, om32)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+
+    def call():
+        swe.diagnostics_noalloc(planes[0].data_ptr(), planes[1].data_ptr(), planes[2].data_ptr(),
+                                H.data_ptr(), nx, ny, nx, nx + 1, wl.dx, wl.dy, out.data_ptr(),
+                                g=wl.params.g, kappa=wl.params.kappa)
+        torch.cuda.synchronize()
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    out.fill_(float("nan"))
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    got = out.cpu().numpy()
+    om = oracle_mod.Oracle(wl).diagnostics(*state)
+    assert _close(got[0], om[0]) and _close(got[1], om[1]), (got, om)
+
+
 def test_noalloc_rejects_too_many_rows(swe):
     import torch
     ny = swe.NOALLOC_MAX_ROWS + 1
