@@ -240,7 +240,8 @@ def use_torch_allocator():
 def use_default_allocator():
     """Domains created from now on allocate with cudaMalloc again (domains
     created under another allocator keep returning their buffers to it)."""
-    _check(load().swe_set_allocator(None, None, None), "swe_set_allocator")
+    _check(load().swe_set_allocator(C.cast(None, ALLOC_FN), C.cast(None, FREE_FN), None),
+           "swe_set_allocator")
 
 
 class Domain:
