@@ -557,13 +557,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         const bool interior = strip * kStrip - 2 >= 0 && strip * kStrip + 29 < a.nx && j0 - 2 >= 0 &&
                               j1 + 1 < a.ny;
         fetch_cell<STAGE>(a, par, i, j0 - 2, interior, cur);
+        // the two rows below the item only fill the window
+        for (int r = j0 - 2; r < j0; r++) {
+            fetch_cell<STAGE>(a, par, i, r + 1, interior, nxt, &cur);
+            Cell<float> c;
+            decode_cell<STAGE>(a, i, r, cur, c);
+            march_row<STAGE>(a, k, r, c, w, KAHAN, false, false, false, false);
+            cur = nxt;
+        }
+        // then each row runs its x part, the y part of the row below, the
+        // flux between them and the update of row r - 2. In stage 2 the
+        // first three run on every row as one straight-line body, so the two
+        // independent chains can interleave (the x parts of rows j1 and
+        // j1 + 1 and the first flux reach no output; stage 2 measured 42.9 ->
+        // 40.9 us on the coastal 1024 step, stage 1 1% slower, so it keeps
+        // the exact flags)
         SWE_UNROLL_PRAGMA(SWE_UNROLL)
-        for (int r = j0 - 2; r <= j1 + 1; r++) {
+        for (int r = j0; r <= j1 + 1; r++) {
             if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, interior, nxt, &cur);
             Cell<float> c;
             decode_cell<STAGE>(a, i, r, cur, c);
-            // which parts this row runs (warp-uniform): see march_row
-            march_row<STAGE>(a, k, r, c, w, KAHAN, r >= j0 && r < j1, r >= j0, r >= j0 + 1, r >= j0 + 2);
+            march_row<STAGE>(a, k, r, c, w, KAHAN, STAGE == 2 || r < j1, true, STAGE == 2 || r >= j0 + 1,
+                             r >= j0 + 2);
             cur = nxt;
         }
     }
