@@ -179,13 +179,16 @@ def _code_only(text):
 
 
 def kernel_source_hash():
-    """Hash of the stage-kernel sources' code: a comment edit keeps the
-    committed counters, any code change drops them."""
+    """Hash of the stage-kernel sources' code and of their compile flags: a
+    comment edit keeps the committed counters, any code or flag change drops
+    them."""
+    from paper_1912_02457_gb300 import build
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1912_02457_gb300", "csrc")
     for name in STAGE_KERNEL_SOURCES:
         with open(os.path.join(csrc, name)) as fh:
             h.update(_code_only(fh.read()).encode())
+    h.update(" ".join(build.NVCC_FLAGS[:2] + build.FILE_FLAGS.get("swe_stage_fast.cu", [])).encode())
     return h.hexdigest()[:16]
 
 

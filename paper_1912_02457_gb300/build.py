@@ -22,8 +22,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 # per-file flags: the FP32 fast path uses the approximate reciprocal and
-# square root (about 1 ulp); the reference kernels stay IEEE
-FILE_FLAGS = {"swe_stage_fast.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+# square root (about 1 ulp) and flushes denormal results to zero (FP32
+# values below 1.2e-38, far below any depth, level or momentum the scheme
+# resolves; 4% on the coastal 1024 step); the reference kernels stay IEEE
+FILE_FLAGS = {"swe_stage_fast.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc():

@@ -19,7 +19,8 @@
 //  * this translation unit is built with approximate FP32 reciprocal and
 //    square root (-prec-div=false -prec-sqrt=false): ~2 ulp, far inside the
 //    parity tolerance, and exact zeros stay exact (lake at rest is still
-//    bit-exact).
+//    bit-exact); denormal results flush to zero (-ftz=true: values below
+//    1.2e-38, far below anything the scheme resolves).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
