@@ -232,8 +232,9 @@ def algorithmic_bytes(wl, precision):
     s2 = 12 + 12 + statics + 12                  # Q^n, D1, statics -> Q^{n+1}
     if precision == "f32_kahan":
         s2 += 24                                 # compensation read + write
-    return {"stage1": wet * s1 + land * 4, "stage2": wet * s2 + land * 4, "clock": 0,
-            "per_cell_step_wet": s1 + s2}
+    s0 = 12 + statics                            # the speed pass of the face-speed step reads Q^n
+    return {"stage1": wet * s1 + land * 4, "stage2": wet * s2 + land * 4, "speed": wet * s0 + land * 4,
+            "clock": 0, "per_cell_step_wet": s1 + s2}
 
 
 # ---------------------------------------------------------------------------
@@ -298,6 +299,7 @@ def run_ours(args):
     swe.load()
 
     wl = synth.coastal(1024, 1024, dtype=np.float32)
+    wl.params.cfl_faces = 1 if args.cfl == "faces" else 0
     cells = wl.nx * wl.ny
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -418,7 +420,8 @@ def run_ours(args):
             "ms_per_step": 1e3 * device_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl.nx, wl.ny, args.precision),
+            "config": dict(workload_config(wl.nx, wl.ny, args.precision),
+                           **({"cfl": "face speeds (speed pass before each step)"} if args.cfl == "faces" else {})),
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
@@ -696,6 +699,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("f32", "f32_kahan"), default="f32_kahan")
+    ap.add_argument("--cfl", choices=("cells", "faces"), default="cells",
+                    help="time step from the cell averages (the scheme's reading) or the faces' speeds")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep", "rossby"),

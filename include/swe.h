@@ -83,6 +83,15 @@ typedef struct {
                                domains on the one-thread-per-cell kernels
                                (slower, not batchable), kept so that tests
                                can cross-check the two FP32 kernel sets */
+    int cfl_faces;          /* 0: eq:cfl with the cell-average velocities and
+                               depths of the state (the reading of the scheme);
+                               1: eq:cfl with the faces' one-sided speeds a+, a-
+                               of the state's reconstruction (Kurganov &
+                               Petrova's condition for non-negative depths over
+                               moving wet-dry fronts; an extra launch per step
+                               and, on drying shelves, much shorter steps).
+                               FP32 domains on the default kernels only, not
+                               batchable (SWE_ERR_UNSUPPORTED otherwise) */
 } swe_params;
 
 /* Domain description. Arrays are read once by swe_create_domain and

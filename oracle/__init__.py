@@ -141,7 +141,7 @@ class Oracle:
             D.bnd_n, D.bnd_nbx, D.bnd_nby = len(bt), wl.boundary.nfx, wl.boundary.nfy
             D.bnd_t, D.bnd = _p(bt), _p(bv)
         D.round_state_f32 = int(bool(round_state_f32))
-        D.cfl_faces = int(bool(cfl_faces))
+        D.cfl_faces = int(bool(cfl_faces or getattr(p, "cfl_faces", 0)))
         self.D = D
         self.L = lib()
 

@@ -100,7 +100,7 @@ struct swe_domain {
     std::vector<ItemList> item_lists;
 
     bool fast() const { return prec != SWE_F64 && p.kernel == 0; }
-    int parts() const { return fast() ? swe::fast_step_parts() : swe::ref_step_parts(); }
+    int parts() const { return fast() ? swe::fast_step_parts(p.cfl_faces != 0) : swe::ref_step_parts(); }
 
     void *dalloc(size_t bytes) {
         void *ptr = nullptr;
@@ -201,6 +201,7 @@ StageArgs<T> make_args(const swe_domain *d) {
     a.clk.wind_uniform = (d->wind_n1 == 1 && d->wind_n2 == 1) ? 1 : 0;
     a.clk.rho_ratio = d->p.rho_air / d->p.rho_water;
     a.clk.fp32 = d->prec == SWE_F64 ? 0 : 1;
+    a.clk.cfl_faces = d->p.cfl_faces;
     return a;
 }
 
@@ -419,6 +420,8 @@ int validate(const swe_domain_desc *d, const swe_params *p) {
     if (p->cd < 0 || p->theta_mm < 1.0 || p->theta_mm > 2.0) return SWE_ERR_INVALID_ARG;
     if (p->dt_fixed < 0 || !(p->rho_water > 0) || p->rho_air < 0) return SWE_ERR_INVALID_ARG;
     if (p->kernel != 0 && p->kernel != 1) return SWE_ERR_INVALID_ARG;
+    if (p->cfl_faces != 0 && p->cfl_faces != 1) return SWE_ERR_INVALID_ARG;
+    if (p->cfl_faces && (d->precision == SWE_F64 || p->kernel != 0)) return SWE_ERR_UNSUPPORTED;
     return SWE_OK;
 }
 
@@ -467,6 +470,7 @@ void swe_default_params(swe_params *p) {
     p->rho_water = 1025.0;
     p->t0 = 0.0;
     p->kernel = 0;
+    p->cfl_faces = 0;
 }
 
 int swe_create_domain(const swe_domain_desc *d, const swe_params *p, void *stream, swe_handle *out) {
@@ -537,7 +541,7 @@ int step_check(swe_handle h, int n_steps) {
 int launch_part_on(swe_handle h, int part, cudaStream_t st) {
     cudaError_t e;
     if (h->prec == SWE_F64) e = swe::launch_step_ref_part(make_args<double>(h), st, part, false);
-    else if (h->fast()) e = swe::launch_domain_stage(h->one, part + 1, st);
+    else if (h->fast()) e = swe::launch_domain_stage(h->one, h->p.cfl_faces ? part : part + 1, st);
     else e = swe::launch_step_ref_part(make_args<float>(h), st, part, h->prec == SWE_F32_KAHAN);
     if (e != cudaSuccess) return cuda_fail(e);
     return SWE_OK;
@@ -598,7 +602,7 @@ int swe_launches_per_step(swe_handle h) {
 
 const char *swe_launch_name(swe_handle h, int part) {
     if (!h) return "";
-    return h->fast() ? swe::fast_part_name(part) : swe::ref_part_name(part);
+    return h->fast() ? swe::fast_part_name(part, h->p.cfl_faces != 0) : swe::ref_part_name(part);
 }
 
 int swe_step_profiled(swe_handle h, int n_steps, float *ms, int capacity) {
@@ -930,7 +934,7 @@ int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out) {
 
 int swe_batch_add(swe_batch_handle b, swe_handle d) {
     if (!b || !d) return SWE_ERR_INVALID_ARG;
-    if (d->prec == SWE_F64 || !d->fast()) return SWE_ERR_UNSUPPORTED;
+    if (d->prec == SWE_F64 || !d->fast() || d->p.cfl_faces) return SWE_ERR_UNSUPPORTED;
     if ((int)b->doms.size() >= b->cap) return SWE_ERR_INVALID_ARG;
     for (swe_handle x : b->doms)
         if (x == d) return SWE_ERR_INVALID_ARG;

@@ -151,10 +151,11 @@ __device__ __forceinline__ Face<T> mirror(Face<T> F) {
 // against the matching part of the bed term). out = flux along DIR.
 template <typename T, int DIR>
 __device__ __forceinline__ void cu_flux(const Face<T> &L, const Face<T> &R, T Hf, T g,
-                                        T out[3]) {
+                                        T out[3], T *speed = nullptr) {
     T unL = DIR == 0 ? L.u : L.v, unR = DIR == 0 ? R.u : R.v;
     T ap = fmax(fmax(unL + L.c, unR + R.c), T(0));
     T am = fmin(fmin(unL - L.c, unR - R.c), T(0));
+    if (speed) *speed = fmax(ap, -am);      // the face's largest one-sided speed
     T den = ap - am;
     T pL = T(0.5) * g * L.eta * (L.eta + T(2) * Hf);
     T pR = T(0.5) * g * R.eta * (R.eta + T(2) * Hf);
@@ -419,9 +420,12 @@ __device__ __forceinline__ void bracket_pre(const double *times, int n, double t
     bracket(times, n, t, k, s, fp32);
 }
 
-// Advance (mode 1) or set up (mode 0: dt from `speed`; mode 2: brackets
-// only) the clock from its loaded inputs. It runs on one thread; the state
-// is written once at the end.
+// The clock from its loaded inputs, on one thread; the state is written
+// once at the end. Modes: 0 set up (dt from `speed`); 1 end of a step (t +=
+// dt, the next dt from `speed`, the cell-average reading of eq:cfl); 2
+// brackets only; 3 the face-speed reading of eq:cfl, before a step (dt from
+// `speed` = the largest face speed over the cell size, no advance); 4 end of
+// a step whose next dt comes from a mode-3 pass (t += dt only).
 __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
                                      const ForcingDev &wind, double speed, int mode, const ClockIn &c) {
     double t = c.t, dt = c.dt;
@@ -429,10 +433,10 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
     int parity = c.parity, done = c.done;
     const double t_end = c.t_end;
     bool bad_speed = false;
-    if (mode == 1) { t += dt; step += 1; parity ^= 1; }
+    if (mode == 1 || mode == 4) { t += dt; step += 1; parity ^= 1; }
     if (clk.dt_fixed > 0.0) {
         dt = clk.dt_fixed;
-    } else if (mode == 0 || (mode == 1 && (clk.dt_every == 1 || step % clk.dt_every == 0))) {
+    } else if (mode == 0 || ((mode == 1 || mode == 3) && (clk.dt_every == 1 || step % clk.dt_every == 0))) {
         if (speed > 0.0 && isfinite(speed)) dt = clk.courant * 0.25 / speed;
         else bad_speed = true;
     }

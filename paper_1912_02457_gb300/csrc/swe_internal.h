@@ -47,6 +47,7 @@ struct ClockParams {
     int wind_uniform;         // wind frames are 1x1: precompute tau per stage
     double rho_ratio;         // rho_air / rho_water
     int fp32;                 // an FP32 domain: frame weights and wind stress in FP32
+    int cfl_faces;            // dt from the faces' one-sided speeds (a speed pass per step)
 };
 
 struct ForcingDev {

@@ -25,11 +25,14 @@ cudaError_t launch_read_plane(const StepCtl *ctl, const T *q0, const T *q1, long
                               int nx, int ny, T *dst, cudaStream_t st);
 
 // FP32 sliding-window stage kernels (swe_stage_fast.cu): stage 1, then
-// stage 2 with the fused CFL reduction and clock update. A single domain
+// stage 2 with the fused CFL reduction and clock update (stage 0: the speed
+// pass of the face-speed time step). A single domain
 // runs through the same kernel as a batch, its arguments in the launch's
 // parameter space.
-int fast_step_parts();
-const char *fast_part_name(int part);
+// With faces: a speed pass (the faces' one-sided speeds of the state, dt)
+// before the two stages.
+int fast_step_parts(bool faces);
+const char *fast_part_name(int part, bool faces);
 // Work planning (swe_stage_fast.cu): a warp item is a strip of 28 output
 // columns by a run of rows, packed as {strip, j0 | rows << 16}; a launch
 // covers the items of the domain's plan. Budgets cap the cost of an item in

@@ -184,7 +184,7 @@ __device__ __forceinline__ void fetch_cell(const StageArgs<float> &a, int par, i
     int pe = 0, ne = 0;
     if (e >= 0) {
         ne = e < 2 ? nx : ny;
-        pe = (STAGE == 1 ? par : par ^ 1) * 12 * (nx + ny) + edge_base(e, nx, ny) + 3 * ring * ne +
+        pe = (STAGE != 2 ? par : par ^ 1) * 12 * (nx + ny) + edge_base(e, nx, ny) + 3 * ring * ne +
              (e >= EDGE_W ? r : i);
     }
     if (!(SWE_CHECK(a, h0, a.n_corner) && SWE_CHECK(a, h0 + cp + 1, a.n_corner) && SWE_CHECK(a, s, a.n_plane) &&
@@ -279,7 +279,7 @@ __device__ __forceinline__ Face<float> shfl_dn_face(const Face<float> &F) {
 
 // Advance the device clock after the last block of stage 2 (clock_update in
 // swe_device.cuh).
-__device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks) {
+__device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks, int mode) {
     if (threadIdx.x != 0) return;
     atomicMax(&a.ctl->speed32, __float_as_uint(block_speed));
     __threadfence();                           // the block's maximum lands before its count
@@ -294,7 +294,7 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nb
     // maximum; the next kernel sees the clock's writes (kernel boundary)
     const unsigned int bits = atomicExch(&a.ctl->speed32, 0u);
     a.ctl->blocks_done = 0u;
-    clock_advance(a.ctl, a.clk, a.bnd, a.wind, (double)__uint_as_float(bits), 1, c);
+    clock_advance(a.ctl, a.clk, a.bnd, a.wind, (double)__uint_as_float(bits), mode, c);
 }
 
 }  // namespace
@@ -314,6 +314,7 @@ struct Window {
     Face<float> savedN;            // finished north face of row r-2
     float Gprev[3];                // y-flux across the south face of row r-2
     float speed;                   // running CFL maximum (stage 2)
+    float fx, fy;                  // largest one-sided face speeds along x and y (speed pass)
 };
 
 // One row of the march: the x-part of row r (X), the y-reconstruction of
@@ -345,6 +346,7 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
     }
 
     // ---- x: reconstruction, fluxes and cell sources of row r
+    float Fe[3] = {0.f, 0.f, 0.f}, etaE = 0.f, etaW = 0.f;
     if (X) {
         Cell<float> L, R;
         L.land = __shfl_up_sync(0xffffffffu, c.land, 1);
@@ -355,7 +357,8 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
         R.fvx = shfl_dn1(c.fvx);
         Face<float> pE, pW;
         reconstruct<float, 0>(L, c, R, a.kx, a.tm, pE, pW);
-        const float etaE = pE.eta, etaW = pW.eta;
+        etaE = pE.eta;
+        etaW = pW.eta;
         finish_face(pE, g, kappa, hik);
         finish_face(pW, g, kappa, hik);
         // east face of this lane: (own E face | west face of lane + 1)
@@ -363,10 +366,20 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
         const float HWr = shfl_dn1(c.HW);
         Face<float> lf = c.land ? mirror<float, 0>(nW) : pE;
         Face<float> rf = R.land ? mirror<float, 0>(pE) : nW;
-        float Fe[3];
-        cu_flux<float, 0>(lf, rf, c.land ? HWr : c.HE, g, Fe);
+        float sp;
+        cu_flux<float, 0>(lf, rf, c.land ? HWr : c.HE, g, Fe, &sp);
         const bool none = c.land && R.land;
         Fe[0] = none ? 0.f : Fe[0]; Fe[1] = none ? 0.f : Fe[1]; Fe[2] = none ? 0.f : Fe[2];
+        if (STAGE == 0) {
+            // the speed pass: the east faces of lanes 1 .. 29 are the strip's
+            // x-faces, those of cells -1 .. nx-1 the domain's (a face with
+            // land on both sides carries no flux and no speed)
+            const bool face = k.lane >= 1 && k.lane <= kStrip + 1 && k.i >= -1 && k.i < a.nx && !none;
+            w.fx = fmaxf(w.fx, face ? sp : 0.f);
+        }
+    }
+    // the x-flux difference and the cell sources (not in the speed pass)
+    if (STAGE != 0 && X) {
         float Fw[3];
         Fw[0] = shfl_up1(Fe[0]); Fw[1] = shfl_up1(Fe[1]); Fw[2] = shfl_up1(Fe[2]);
         acc0[0] = -(Fe[0] - Fw[0]) * a.inv_dx;
@@ -404,12 +417,21 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
             // face between rows r-2 (A, north face savedN) and r-1 (B)
             Face<float> lf = w.A.land ? mirror<float, 1>(pS) : w.savedN;
             Face<float> rf = w.B.land ? mirror<float, 1>(w.savedN) : pS;
-            cu_flux<float, 1>(lf, rf, w.B.land ? w.A.HN : w.B.HS, g, Gcur);
+            float sp;
+            cu_flux<float, 1>(lf, rf, w.B.land ? w.A.HN : w.B.HS, g, Gcur, &sp);
             const bool none = w.A.land && w.B.land;
             Gcur[0] = none ? 0.f : Gcur[0]; Gcur[1] = none ? 0.f : Gcur[1]; Gcur[2] = none ? 0.f : Gcur[2];
+            if (STAGE == 0) {
+                // the speed pass: the faces below the item's rows and above
+                // them (rows j0-1 | j0 .. j1-1 | j1) of the strip's own
+                // columns inside the domain
+                const bool face = k.out_lane && k.i >= 0 && !none;
+                w.fy = fmaxf(w.fy, face ? sp : 0.f);
+            }
         }
         // bed term of row r-1 in y (it is an output row whenever G and r-1 < j1)
-        if (G && r - 1 < k.j1) w.acc1[2] += g * 0.5f * (etaN + etaS) * (w.B.HN - w.B.HS) * a.inv_dy;
+        if (STAGE != 0 && G && r - 1 < k.j1)
+            w.acc1[2] += g * 0.5f * (etaN + etaS) * (w.B.HN - w.B.HS) * a.inv_dy;
         w.savedN = pN;
     }
 
@@ -513,7 +535,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     const StepCtl *ctl = a.ctl;
     const int done = ctl->done, par = ctl->parity;
     const double dt = ctl->dt;
-    const float taux = ctl->tau_f[STAGE - 1][0], tauy = ctl->tau_f[STAGE - 1][1];
+    const float taux = STAGE == 0 ? 0.f : ctl->tau_f[STAGE - 1][0];
+    const float tauy = STAGE == 0 ? 0.f : ctl->tau_f[STAGE - 1][1];
     if (done) return;                              // forecast horizon reached (block-uniform)
     StripCtx k;
     k.lane = lane;
@@ -550,6 +573,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     w.S1 = w.S2 = 0.f;
     w.savedN.h = w.savedN.eta = w.savedN.hu = w.savedN.hv = w.savedN.u = w.savedN.v = w.savedN.c = 0.f;
     w.speed = 0.f;
+    w.fx = w.fy = 0.f;
 
     if (strip_live) {
         const int i = k.i, j0 = k.j0, j1 = k.j1, par = k.par;
@@ -579,21 +603,24 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
             Cell<float> c;
             decode_cell<STAGE>(a, i, r, cur, c);
             march_row<STAGE>(a, k, r, c, w, KAHAN, STAGE == 2 || r < j1, true, STAGE == 2 || r >= j0 + 1,
-                             r >= j0 + 2);
+                             STAGE != 0 && r >= j0 + 2);
             cur = nxt;
         }
     }
 
-    if (STAGE == 2) {
+    if (STAGE == 0 || STAGE == 2) {
+        // stage 2: the CFL maximum of the cells (eq:cfl with the cell
+        // averages); the speed pass: the largest face speed over the cell
+        // size (eq:cfl with the faces' one-sided speeds)
         __shared__ float sh[kWarps];
-        float speed = w.speed;
+        float speed = STAGE == 0 ? fmaxf(w.fx * a.inv_dx, w.fy * a.inv_dy) : w.speed;
         for (int o = 16; o > 0; o >>= 1) speed = fmaxf(speed, __shfl_xor_sync(0xffffffffu, speed, o));
         if (lane == 0) sh[warp] = speed;
         __syncthreads();
         float bs = 0.f;
         if (threadIdx.x == 0)
             for (int q = 0; q < kWarps; q++) bs = fmaxf(bs, sh[q]);
-        finish_step(a, bs, nblocks);
+        finish_step(a, bs, nblocks, STAGE == 0 ? 3 : (a.clk.cfl_faces ? 4 : 1));
     }
 }
 
@@ -847,11 +874,12 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
     items.swap(out);
 }
 
-int fast_step_parts() { return 2; }
+int fast_step_parts(bool faces) { return faces ? 3 : 2; }
 
-const char *fast_part_name(int part) {
-    static const char *names[2] = {"stage1", "stage2"};
-    return part >= 0 && part < 2 ? names[part] : "";
+const char *fast_part_name(int part, bool faces) {
+    static const char *names[3] = {"speed", "stage1", "stage2"};
+    if (faces) return part >= 0 && part < 3 ? names[part] : "";
+    return part >= 0 && part < 2 ? names[part + 1] : "";
 }
 
 // Blocks (of kWarps warp items) a launch over n_items items needs.
@@ -915,8 +943,9 @@ static cudaError_t launch_stage(int stage, int blocks, const BatchTable &tab, co
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = stage == 1 ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<1>, tab, one)
-                               : cudaLaunchKernelEx(&cfg, stage_batch_kernel<2>, tab, one);
+    cudaError_t e = stage == 0   ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<0>, tab, one)
+                    : stage == 1 ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<1>, tab, one)
+                                 : cudaLaunchKernelEx(&cfg, stage_batch_kernel<2>, tab, one);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -38,7 +38,8 @@ class Params(C.Structure):
                 ("cd", C.c_double), ("courant", C.c_double), ("frs_d0", C.c_double),
                 ("frs_width", C.c_int), ("dt_update_every", C.c_int),
                 ("dt_fixed", C.c_double), ("rho_air", C.c_double),
-                ("rho_water", C.c_double), ("t0", C.c_double), ("kernel", C.c_int)]
+                ("rho_water", C.c_double), ("t0", C.c_double), ("kernel", C.c_int),
+                ("cfl_faces", C.c_int)]
 
 
 class DomainDesc(C.Structure):
@@ -214,6 +215,7 @@ def params_from(wl_params, t0=0.0, kernel=0) -> Params:
         setattr(p, k, getattr(wl_params, k))
     p.t0 = t0
     p.kernel = kernel
+    p.cfl_faces = int(getattr(wl_params, "cfl_faces", 0))
     return p
 
 

@@ -56,6 +56,7 @@ class Params:
     dt_fixed: float = 0.0        # > 0: fixed time step
     rho_air: float = 1.225
     rho_water: float = 1025.0
+    cfl_faces: int = 0           # 1: time step from the faces' one-sided speeds
 
 
 @dataclasses.dataclass

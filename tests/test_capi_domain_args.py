@@ -99,9 +99,25 @@ def test_periodic_corner_plane_must_repeat_its_first_line(L):
 @pytest.mark.parametrize("field,value", [("g", 0.0), ("kappa", -1.0), ("courant", 0.0),
                                          ("theta_mm", 0.5), ("theta_mm", 2.5), ("frs_width", 33),
                                          ("frs_d0", 0.0), ("cd", -0.1), ("dt_fixed", -1.0),
-                                         ("rho_water", 0.0), ("kernel", 3)])
+                                         ("rho_water", 0.0), ("kernel", 3), ("cfl_faces", 2)])
 def test_out_of_range_parameters(L, field, value):
     keep = []
     p = swe.default_params()
     setattr(p, field, value)
     assert _create(L, _desc(keep=keep), p) == INVALID
+
+
+@pytest.mark.parametrize("precision,kernel", [(2, 0), (0, 1), (1, 1)])
+def test_face_speed_step_needs_the_fp32_default_kernels(L, precision, kernel):
+    """The face-speed time step exists on the FP32 default kernels only."""
+    keep = []
+    d = _desc(keep=keep)
+    d.precision = precision
+    if precision == 2:                           # FP64 inputs are doubles
+        H = np.full(((d.ny + 1) * (d.nx + 1),), 10.0)
+        keep.append(H)
+        d.H = H.ctypes.data
+    p = swe.default_params()
+    p.kernel = kernel
+    p.cfl_faces = 1
+    assert _create(L, d, p) == swe.ERR_UNSUPPORTED
