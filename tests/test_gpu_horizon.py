@@ -9,10 +9,14 @@ Parity is gated at 1000 steps elsewhere. Over the full horizon the moving
 wet-dry fronts of this recipe produce what Section 3.4 warns of (non-physical
 waves and small time steps): thin drying films on raised shelves carry
 momentum, their desingularised velocities spike, and the CFL step drops to
-below a millisecond at times, in the oracle as on the GPU. After the first
-such event runs that differ by rounding take different step sequences, so
-the end states differ at the level of the waves themselves (the FP64 GPU
-path, within 1e-11 of the oracle per step, ends as far from it as FP32).
+a few hundredths of a second at times, in the oracle as on the GPU. The
+mechanism is pinned in test_oracle_positivity.py: the cell-average time
+step exceeds the faces' one-sided speeds there by a factor of ten or more,
+so Kurganov & Petrova's condition for non-negative depths fails. After the
+first such event runs that differ by rounding take different step
+sequences, so the end states differ at the level of the waves themselves
+(the FP64 GPU path, within 1e-11 of the oracle per step, ends as far from
+it as FP32).
 The moving-front test therefore reports the deviation and checks only
 that a run is sound: finite, no sticky error, the exact end time, a step
 count close to the oracle's, and deviations below the size of the
