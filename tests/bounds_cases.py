@@ -1,6 +1,7 @@
 """Cases run against the bounds-checked library (SWE_LIBRARY points at it):
 tiny odd grids with every boundary kind, land across strips, a spatially
-varying wind, flow relaxation, a batch of mixed domains, both FP32 modes.
+varying wind, flow relaxation, a batch of mixed domains, both FP32 modes,
+each also with the face-speed time step (its speed pass).
 Prints one JSON object: case name -> [status of swe_get_info, error_cell]."""
 import json
 import os
@@ -53,6 +54,15 @@ def main():
             st = swe.load().swe_get_info(d.h, swe.C.byref(i))
             res[f"{name} {prec}"] = [int(st), int(i.error_cell)]
             doms.append((name, wl))
+            d.close()
+            # the face-speed time step (its speed pass reads the same cells)
+            wf = wl.copy()
+            wf.params.cfl_faces = 1
+            d = swe.Domain(wf, prec)
+            d.step(7)
+            i = d.info(check=False)
+            st = swe.load().swe_get_info(d.h, swe.C.byref(i))
+            res[f"{name} {prec} faces"] = [int(st), int(i.error_cell)]
             d.close()
         # the same domains in one batch
         b = swe.Batch()
