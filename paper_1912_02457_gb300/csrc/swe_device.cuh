@@ -335,22 +335,31 @@ __device__ inline void flag_error(StepCtl *ctl, int cell) {
 // runs in translation units built with different division, square-root and
 // contraction settings, and must give the same bits in all of them (a
 // resumed run replays the clock of an uninterrupted one).
-__device__ __forceinline__ double frame_weight(double off, double len, bool fp32) {
-    return fp32 ? (double)__fdiv_rn((float)off, (float)len) : off / len;
+// The frame weight: in FP64, or (fp32) as the FP32 quotient of the FP64
+// offset and interval rounded once each; *sf holds it in FP32 either way.
+__device__ __forceinline__ void frame_weight(double off, double len, bool fp32, double *s, float *sf) {
+    if (fp32) {
+        *sf = __fdiv_rn((float)off, (float)len);
+        *s = (double)*sf;
+    } else {
+        *s = off / len;
+        *sf = (float)*s;
+    }
 }
 
 __device__ __forceinline__ void bracket(const double *times, int n, double t, int *k, double *s,
-                                        bool fp32) {
+                                        float *sf, bool fp32) {
+    *sf = 0.f;
     if (n <= 1) { *k = 0; *s = 0.0; return; }
     if (t <= times[0]) { *k = 0; *s = 0.0; return; }
-    if (t >= times[n - 1]) { *k = n - 2; *s = 1.0; return; }
+    if (t >= times[n - 1]) { *k = n - 2; *s = 1.0; *sf = 1.f; return; }
     int lo = 0, hi = n - 1;            // times[lo] <= t < times[hi]
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (times[mid] <= t) lo = mid; else hi = mid;
     }
     *k = lo;
-    *s = frame_weight(t - times[lo], times[lo + 1] - times[lo], fp32);
+    frame_weight(t - times[lo], times[lo + 1] - times[lo], fp32, s, sf);
 }
 
 // The clock's inputs: its state of the previous step and the forcing values
@@ -363,6 +372,11 @@ struct ClockIn {
     long long step;
     int parity, done;
     int bhint, whint;          // bracket of the previous stage-2 time
+    // the brackets and uniform wind stress at this step's stage-1 time as
+    // the previous evaluation left them (see clock_advance)
+    int ck_b, ck_w;
+    double cs_b, cs_w, ctau[2];
+    float cs_b_f, ctau_f[2];
     double bt0, bt1;           // boundary times[bhint], times[bhint + 1] (if a bracket)
     double wt0, wt1;           // wind times around whint (if a bracket)
     int wk_pre;                // wind frame whose uniform values follow (-1: none)
@@ -373,8 +387,10 @@ __device__ __forceinline__ bool hint_ok(const ForcingDev &F, int hint) {
     return F.n > 1 && hint >= 0 && hint < F.n - 1;
 }
 
-// First level: the clock state (one round of independent loads).
-__device__ __forceinline__ void clock_load_state(const StepCtl *ctl, ClockIn &c) {
+// First level: the clock state (one round of independent loads). `mode` as
+// in clock_advance: the values at the stage-1 time of the step it sets up
+// are the previous stage-2 ones (modes 1, 4) or stage-1 ones (mode 3).
+__device__ __forceinline__ void clock_load_state(const StepCtl *ctl, ClockIn &c, int mode) {
     c.t = ctl->t;
     c.dt = ctl->dt;
     c.t_end = ctl->t_end;
@@ -383,6 +399,16 @@ __device__ __forceinline__ void clock_load_state(const StepCtl *ctl, ClockIn &c)
     c.done = ctl->done;
     c.bhint = ctl->bk[1];
     c.whint = ctl->wk[1];
+    const int src = mode == 3 ? 0 : 1;
+    c.ck_b = ctl->bk[src];
+    c.ck_w = ctl->wk[src];
+    c.cs_b = ctl->bs[src];
+    c.cs_w = ctl->ws[src];
+    c.ctau[0] = ctl->tau[src][0];
+    c.ctau[1] = ctl->tau[src][1];
+    c.cs_b_f = ctl->bs_f[src];
+    c.ctau_f[0] = ctl->tau_f[src][0];
+    c.ctau_f[1] = ctl->tau_f[src][1];
 }
 
 // Second level: the frame times around the previous brackets and the
@@ -411,13 +437,13 @@ __device__ __forceinline__ void clock_load_forcing(const ClockParams &clk, const
 // interval (all an FP32 domain uses; the FP64 division is slow on GB300),
 // and s holds it widened.
 __device__ __forceinline__ void bracket_pre(const double *times, int n, double t, int hint, double t0,
-                                            double t1, int *k, double *s, bool fp32) {
+                                            double t1, int *k, double *s, float *sf, bool fp32) {
     if (n > 1 && hint >= 0 && hint < n - 1 && t0 <= t && t < t1) {
         *k = hint;
-        *s = frame_weight(t - t0, t1 - t0, fp32);
+        frame_weight(t - t0, t1 - t0, fp32, s, sf);
         return;
     }
-    bracket(times, n, t, k, s, fp32);
+    bracket(times, n, t, k, s, sf, fp32);
 }
 
 // The clock from its loaded inputs, on one thread; the state is written
@@ -432,11 +458,15 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
     long long step = c.step;
     int parity = c.parity, done = c.done;
     const double t_end = c.t_end;
+    const bool fp32 = clk.fp32 != 0;
     bool bad_speed = false;
     if (mode == 1 || mode == 4) { t += dt; step += 1; parity ^= 1; }
     if (clk.dt_fixed > 0.0) {
         dt = clk.dt_fixed;
     } else if (mode == 0 || ((mode == 1 || mode == 3) && (clk.dt_every == 1 || step % clk.dt_every == 0))) {
+        // eq:cfl, the FP64 quotient. (An FP32 quotient saves ~0.2 us of the
+        // stage-2 tail but moved the 24 h static-coast run from 7.8e-6 to
+        // 1.2e-4 m off the oracle: dt is kept exact.)
         if (speed > 0.0 && isfinite(speed)) dt = clk.courant * 0.25 / speed;
         else bad_speed = true;
     }
@@ -447,12 +477,27 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
     }
     int bk[2], wk[2];
     double bs[2], ws[2], tau[2][2];
-    const bool fp32 = clk.fp32 != 0;
-    for (int q = 0; q < 2; q++) {
+    float bs_f[2], ws_f[2], tau_f[2][2];
+    // The stage-1 time of the step being set up is the time at which the
+    // previous evaluation took its stage-2 values (modes 1, 4: the new t is
+    // the same FP64 sum t + dt that evaluation formed) or its stage-1 values
+    // (mode 3: t does not move). Brackets, weights and stress at a given
+    // time are unique, so they are carried over, bit for bit, and only the
+    // stage-2 time, which depends on the new dt, is evaluated here. (Forcing
+    // replaced in between goes through mode 2, which evaluates both.)
+    const bool carry = mode == 1 || mode == 3 || mode == 4;
+    if (carry) {
+        bk[0] = c.ck_b; bs[0] = c.cs_b; bs_f[0] = c.cs_b_f;
+        wk[0] = c.ck_w; ws[0] = c.cs_w; ws_f[0] = 0.f;
+        tau[0][0] = c.ctau[0]; tau[0][1] = c.ctau[1];
+        tau_f[0][0] = c.ctau_f[0]; tau_f[0][1] = c.ctau_f[1];
+    }
+    for (int q = carry ? 1 : 0; q < 2; q++) {
         const double tt = t + (q ? dt : 0.0);
-        bracket_pre(bnd.times, bnd.n, tt, c.bhint, c.bt0, c.bt1, &bk[q], &bs[q], fp32);
-        bracket_pre(wind.times, wind.n, tt, c.whint, c.wt0, c.wt1, &wk[q], &ws[q], fp32);
+        bracket_pre(bnd.times, bnd.n, tt, c.bhint, c.bt0, c.bt1, &bk[q], &bs[q], &bs_f[q], fp32);
+        bracket_pre(wind.times, wind.n, tt, c.whint, c.wt0, c.wt1, &wk[q], &ws[q], &ws_f[q], fp32);
         tau[q][0] = tau[q][1] = 0.0;
+        tau_f[q][0] = tau_f[q][1] = 0.f;
         if (wind.n > 0 && clk.wind_uniform) {
             float a0 = c.wa[0], a1 = c.wa[1], b0 = c.wb[0], b1 = c.wb[1];
             if (wk[q] != c.wk_pre) {
@@ -463,14 +508,16 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
             if (fp32) {
                 // Large & Pond stress (Section 3.5) in the precision the FP32
                 // stage kernels use it in
-                const float w = (float)ws[q], w1 = __fsub_rn(1.f, w);
+                const float w = ws_f[q], w1 = __fsub_rn(1.f, w);
                 const float wx = __fadd_rn(__fmul_rn(w1, a0), __fmul_rn(w, b0));
                 const float wy = __fadd_rn(__fmul_rn(w1, a1), __fmul_rn(w, b1));
                 const float sp = __fsqrt_rn(__fadd_rn(__fmul_rn(wx, wx), __fmul_rn(wy, wy)));
                 const float cdrag = sp < 11.f ? 1.2e-3f : __fmul_rn(__fadd_rn(0.49f, __fmul_rn(0.065f, sp)), 1e-3f);
                 const float k = __fmul_rn(__fmul_rn((float)clk.rho_ratio, cdrag), sp);
-                tau[q][0] = __fmul_rn(k, wx);
-                tau[q][1] = __fmul_rn(k, wy);
+                tau_f[q][0] = __fmul_rn(k, wx);
+                tau_f[q][1] = __fmul_rn(k, wy);
+                tau[q][0] = (double)tau_f[q][0];
+                tau[q][1] = (double)tau_f[q][1];
             } else {
                 double w = ws[q];
                 double wx = (1.0 - w) * a0 + w * b0;
@@ -480,6 +527,8 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
                 double k = clk.rho_ratio * cdrag * sp;
                 tau[q][0] = k * wx;
                 tau[q][1] = k * wy;
+                tau_f[q][0] = (float)tau[q][0];
+                tau_f[q][1] = (float)tau[q][1];
             }
         }
     }
@@ -496,16 +545,16 @@ __device__ inline void clock_advance(StepCtl *ctl, const ClockParams &clk, const
         ctl->bk[q] = bk[q]; ctl->bs[q] = bs[q];
         ctl->wk[q] = wk[q]; ctl->ws[q] = ws[q];
         ctl->tau[q][0] = tau[q][0]; ctl->tau[q][1] = tau[q][1];
-        ctl->bs_f[q] = (float)bs[q];
-        ctl->tau_f[q][0] = (float)tau[q][0];
-        ctl->tau_f[q][1] = (float)tau[q][1];
+        ctl->bs_f[q] = bs_f[q];
+        ctl->tau_f[q][0] = tau_f[q][0];
+        ctl->tau_f[q][1] = tau_f[q][1];
     }
 }
 
 __device__ inline void clock_update(StepCtl *ctl, const ClockParams &clk, const ForcingDev &bnd,
                                     const ForcingDev &wind, double speed, int mode) {
     ClockIn c;
-    clock_load_state(ctl, c);
+    clock_load_state(ctl, c, mode);
     clock_load_forcing(clk, bnd, wind, c);
     clock_advance(ctl, clk, bnd, wind, speed, mode, c);
 }

@@ -286,7 +286,7 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nb
     // every block loads the clock's inputs while its count is in flight;
     // the last one then needs no further round trip to memory
     ClockIn c;
-    clock_load_state(a.ctl, c);
+    clock_load_state(a.ctl, c, mode);
     const unsigned int prev = atomicAdd(&a.ctl->blocks_done, 1u);
     clock_load_forcing(a.clk, a.bnd, a.wind, c);
     if (prev != (unsigned int)nblocks - 1u) return;
