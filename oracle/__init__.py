@@ -52,6 +52,7 @@ class _Domain(C.Structure):
         ("bnd_t", C.POINTER(C.c_double)), ("bnd", C.POINTER(C.c_double)),
         ("round_state_f32", C.c_int),
         ("cfl_faces", C.c_int),
+        ("off_x", C.c_int), ("off_y", C.c_int), ("gnx", C.c_int), ("gny", C.c_int),
     ]
 
 
@@ -79,6 +80,8 @@ def lib():
             L.orc_ghosts.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, _dp]
             L.orc_step.restype = C.c_int
             L.orc_step.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double, C.c_double]
+            L.orc_frs.restype = None
+            L.orc_frs.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp, C.c_double]
             L.orc_max_speed.restype = C.c_double
             L.orc_max_speed.argtypes = [C.POINTER(_Domain), _dp, _dp, _dp]
             L.orc_cfl_dt.restype = C.c_double
@@ -110,7 +113,12 @@ def _p(a):
 class Oracle:
     """The oracle bound to one workload's statics and forcing."""
 
-    def __init__(self, wl, round_state_f32: bool = False, cfl_faces: bool = False):
+    def __init__(self, wl, round_state_f32: bool = False, cfl_faces: bool = False,
+                 offset=(0, 0), whole=None):
+        """``offset``, ``whole``: the workload is the window of a larger
+        domain of ``whole`` = (nx, ny) cells whose cell (0, 0) is the whole
+        domain's cell ``offset`` (forcing sampled at the whole domain's
+        positions); by default the workload is the whole domain."""
         self.wl = wl
         p = wl.params
         nx, ny = wl.nx, wl.ny
@@ -142,6 +150,9 @@ class Oracle:
             D.bnd_t, D.bnd = _p(bt), _p(bv)
         D.round_state_f32 = int(bool(round_state_f32))
         D.cfl_faces = int(bool(cfl_faces or getattr(p, "cfl_faces", 0)))
+        D.off_x, D.off_y = int(offset[0]), int(offset[1])
+        if whole is not None:
+            D.gnx, D.gny = int(whole[0]), int(whole[1])
         self.D = D
         self.L = lib()
 
@@ -182,6 +193,13 @@ class Oracle:
         if self.L.orc_face_speeds(C.byref(self.D), _p(e), _p(u), _p(v), t, _p(out)):
             raise MemoryError("oracle face speeds failed")
         return float(out[0]), float(out[1])
+
+    def frs(self, eta, hu, hv, t):
+        """The flow relaxation of eq:frs at time t, applied in place to
+        float64 C-contiguous arrays."""
+        for a in (eta, hu, hv):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+        self.L.orc_frs(C.byref(self.D), _p(eta), _p(hu), _p(hv), float(t))
 
     def max_speed(self, eta, hu, hv):
         e, u, v = _d(eta), _d(hu), _d(hv)

@@ -74,7 +74,18 @@ typedef struct {
      * every cell depth non-negative (used by the pins that show why the
      * cell-average reading does not). */
     int cfl_faces;
+    /* A window of a larger domain (the domain decomposition of the stencil
+     * of Section 3: sub-domains that exchange a two-cell halo per stage):
+     * cell (0, 0) of this domain is cell (off_x, off_y) of a gnx x gny
+     * domain, and the forcing (wind grid, nesting frames along an edge) is
+     * sampled at the whole domain's positions. gnx = gny = 0: the domain is
+     * whole (off_x = off_y = 0). */
+    int off_x, off_y, gnx, gny;
 } orc_domain;
+
+/* the whole domain's extent along x and y */
+static int whole_nx(const orc_domain *d) { return d->gnx > 0 ? d->gnx : d->nx; }
+static int whole_ny(const orc_domain *d) { return d->gny > 0 ? d->gny : d->ny; }
 
 /* ------------------------------------------------------------------------ */
 /* small pieces of the method                                               */
@@ -153,8 +164,8 @@ static void wind_at(const orc_domain *d, int i, int j, double t,
     int k; double s;
     time_bracket(d->wind_t, d->wind_n, t, &k, &s);
     int x0, x1, y0, y1; double wx, wy;
-    axis_lerp(i, d->nx, d->wind_nfx, &x0, &x1, &wx);
-    axis_lerp(j, d->ny, d->wind_nfy, &y0, &y1, &wy);
+    axis_lerp(i + d->off_x, whole_nx(d), d->wind_nfx, &x0, &x1, &wx);
+    axis_lerp(j + d->off_y, whole_ny(d), d->wind_nfy, &y0, &y1, &wy);
     double W[2];
     for (int c = 0; c < 2; c++) {
         double v[2];
@@ -175,12 +186,14 @@ static void wind_at(const orc_domain *d, int i, int j, double t,
 /* External (nesting) value of variable v (0 eta, 1 hu, 2 hv) in ghost row r
  * (0 touching the domain) of edge e at along-edge cell k and time t:
  * linear in time between the bracketing frames and linear along the edge
- * (Section 3.6: the boundary data is interpolated like the wind). */
+ * (Section 3.6: the boundary data is interpolated like the wind). A window
+ * samples the edge at the whole domain's cell k + offset. */
 static double bnd_value(const orc_domain *d, int e, int r, int v, int k, double t)
 {
     int nbx = d->bnd_nbx, nby = d->bnd_nby;
     int nb = (e == ORC_S || e == ORC_N) ? nbx : nby;
-    int n = (e == ORC_S || e == ORC_N) ? d->nx : d->ny;
+    int n = (e == ORC_S || e == ORC_N) ? whole_nx(d) : whole_ny(d);
+    k += (e == ORC_S || e == ORC_N) ? d->off_x : d->off_y;
     size_t off = 0;
     if (e >= ORC_N) off += (size_t)6 * nbx;
     if (e >= ORC_W) off += (size_t)6 * nbx;
@@ -860,6 +873,12 @@ static void apply_frs(const orc_domain *d, double *eta, double *hu, double *hv, 
                 hv[s] = (1.0 - a) * hv[s] + a * bnd_value(d, e, 0, 2, k, t);
             }
     }
+}
+
+/* The flow relaxation of eq:frs at time t (what follows each step). */
+void orc_frs(const orc_domain *d, double *eta, double *hu, double *hv, double t)
+{
+    apply_frs(d, eta, hu, hv, t);
 }
 
 /* One time step of the semi-implicit SSP-RK2 scheme, eq:rk2_semiimp:

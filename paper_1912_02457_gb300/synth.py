@@ -289,6 +289,59 @@ def edge_sample_floor(Hbar: np.ndarray, land: np.ndarray, zone: int, nb_div: int
 # workloads
 # --------------------------------------------------------------------------
 
+def partition(nx: int, ny: int, px: int, py: int, halo: int = 2) -> list:
+    """Split an nx x ny domain into px x py sub-domains for a halo-exchange
+    decomposition (each RK stage of the scheme reads two cells along x and
+    y, so a sub-domain that holds ``halo`` = 2 cells of each neighbour
+    beyond its own cells, refreshed after every stage, updates its own cells
+    exactly as the whole domain would). Integer bookkeeping only.
+
+    Returns one dict per sub-domain, row-major (x fastest):
+    ``own`` (x0, x1, y0, y1), the owned cells in whole-domain coordinates;
+    ``win`` (x0, x1, y0, y1), the window: the owned cells plus ``halo``
+    cells on every side with a neighbour; ``cut`` (S, N, W, E), whether a
+    neighbour lies beyond that edge of the window; ``rank`` its index.
+    Owned extents differ by at most one cell and hold at least ``halo``
+    cells each (so a halo comes from the adjacent sub-domain only)."""
+    if px < 1 or py < 1 or nx < px * halo or ny < py * halo:
+        raise ValueError(f"cannot split {nx}x{ny} into {px}x{py} parts of >= {halo} cells")
+
+    def cuts(n, parts):
+        return [n * k // parts for k in range(parts + 1)]
+
+    xs, ys = cuts(nx, px), cuts(ny, py)
+    out = []
+    for b in range(py):
+        for a in range(px):
+            x0, x1, y0, y1 = xs[a], xs[a + 1], ys[b], ys[b + 1]
+            cut = (b > 0, b < py - 1, a > 0, a < px - 1)
+            win = (x0 - halo * cut[2], x1 + halo * cut[3], y0 - halo * cut[0], y1 + halo * cut[1])
+            out.append({"own": (x0, x1, y0, y1), "win": win, "cut": cut, "rank": b * px + a})
+    return out
+
+
+def window(wl: Workload, part: dict) -> Workload:
+    """The sub-workload of one ``partition`` entry: planes and corner
+    bathymetry cut to the window, the edges that face a neighbour turned
+    into walls (the cells next to them are halo cells, overwritten by the
+    exchange, so what the wall does to them is never used), the whole
+    domain's forcing (sampled at the whole domain's positions by the side
+    that steps the window)."""
+    x0, x1, y0, y1 = part["win"]
+    if any(part["cut"]) and any(b == BC_PERIODIC for b in wl.bc):
+        raise ValueError("periodic edges are not split")
+    c = wl.copy()
+    for k in ("eta", "hu", "hv", "f", "theta"):
+        v = getattr(wl, k)
+        if v is not None:
+            setattr(c, k, np.ascontiguousarray(v[y0:y1, x0:x1]))
+    c.H = np.ascontiguousarray(wl.H[y0:y1 + 1, x0:x1 + 1])
+    c.nx, c.ny = x1 - x0, y1 - y0
+    c.bc = tuple(BC_WALL if part["cut"][e] else wl.bc[e] for e in range(4))
+    c.name = f"{wl.name}[{x0}:{x1},{y0}:{y1}]"
+    return c
+
+
 def gaussian_bump(dtype=np.float32, n: int = 128, steps: int = 1000) -> Workload:
     """Plain method: n x n cells, dx = dy = 800 m, flat 100 m depth, walls,
     f-plane f = 1.2e-4 1/s, north angle 0, no friction or wind, a 1 m
