@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 #define SWE_LAND 3.40282346638528859812e+38f  /* FLT_MAX: land corner */
-#define SWE_ABI_VERSION 1
+#define SWE_ABI_VERSION 2
 
 typedef enum {
     SWE_OK = 0,
@@ -92,6 +92,25 @@ typedef struct {
                                and, on drying shelves, much shorter steps).
                                FP32 domains on the default kernels only, not
                                batchable (SWE_ERR_UNSUPPORTED otherwise) */
+    /* Domain decomposition. Each RK stage of the scheme (Section 3:
+       reconstruction from two cells on each side, fluxes between them)
+       reads two cells along x and along y, so sub-domains that hold a
+       two-cell halo of their neighbours' cells, refreshed after every
+       stage, update their own cells exactly as the whole domain would.
+       whole_nx = whole_ny = 0 (the default): this domain is whole and the
+       other fields below are 0. Otherwise it is the window of a
+       whole_nx x whole_ny domain whose cell (0, 0) is the whole domain's
+       cell (window_x0, window_y0): wind and nesting frames are sampled at
+       the whole domain's positions; it owns the cells [own_x0, own_x1) x
+       [own_y0, own_y1) of the window (window coordinates), and its other
+       cells are halo cells that swe_split_step overwrites from the
+       sub-domains owning them (an edge of the window that faces a
+       neighbour is given as a wall: what it does to the halo cells next
+       to it is never used). Its CFL maximum covers its own cells only.
+       FP32 domains on the default kernels with cfl_faces 0 and no
+       periodic edge (SWE_ERR_UNSUPPORTED otherwise); not batchable. */
+    int window_x0, window_y0, whole_nx, whole_ny;
+    int own_x0, own_x1, own_y0, own_y1;
 } swe_params;
 
 /* Domain description. Arrays are read once by swe_create_domain and
@@ -269,6 +288,32 @@ int swe_batch_poll(swe_batch_handle b, int *done, double *t, int capacity);
 /* Kernel launches issued by this batch so far. */
 long long swe_batch_launches(swe_batch_handle b);
 int swe_batch_destroy(swe_batch_handle b);
+
+/* ---- domain decomposition on one device --------------------------------
+ * n sub-domains (windows created with whole_nx > 0, see swe_params) whose
+ * own cells tile the whole domain exactly once and whose halo cells each
+ * lie in another sub-domain's own cells, all on one stream, with the same
+ * whole domain, cell size, precision and clock parameters; at most
+ * SWE_SPLIT_MAX of them. Both calls are asynchronous on that stream.
+ * swe_split_sync: one clock for all of them: the CFL maximum of eq:cfl
+ * over every sub-domain's own cells sets one initial time step (their
+ * clocks must hold the same t; call it after creating them, and after
+ * swe_set_clock or swe_set_forcing on them).
+ * swe_split_step: n_steps steps of the whole domain: stage 1 of every
+ * sub-domain, the exchange of the stage-1 increment's halo cells, stage 2
+ * of every sub-domain, one clock evaluation from the largest of their CFL
+ * maxima (eq:cfl; every sub-domain gets the same t, dt and forcing
+ * brackets), the exchange of the new state's halo cells. The own cells
+ * end bit for bit where the whole domain's steps put them. The exchanges
+ * are device copies between the sub-domains' planes; the same sequence
+ * across devices would exchange through peer copies or messages (not
+ * provided: one device).
+ * Errors: SWE_ERR_INVALID_ARG (NULL, n out of range, not a tiling,
+ * different streams or parameters, a domain that is not a window),
+ * SWE_ERR_NUMERIC (a sticky device error observed before), SWE_ERR_CUDA. */
+#define SWE_SPLIT_MAX 16
+int swe_split_sync(const swe_handle *doms, int n);
+int swe_split_step(const swe_handle *doms, int n, int n_steps);
 
 /* ---- diagnostics for callers that cannot allocate ----------------------
  * The paper has no counterpart to this function; it is a service of this

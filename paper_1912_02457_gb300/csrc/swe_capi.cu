@@ -202,6 +202,17 @@ StageArgs<T> make_args(const swe_domain *d) {
     a.clk.rho_ratio = d->p.rho_air / d->p.rho_water;
     a.clk.fp32 = d->prec == SWE_F64 ? 0 : 1;
     a.clk.cfl_faces = d->p.cfl_faces;
+    // a window of a larger domain, or the whole domain
+    const bool win = d->p.whole_nx > 0;
+    a.clk.split = win ? 1 : 0;
+    a.off_x = win ? d->p.window_x0 : 0;
+    a.off_y = win ? d->p.window_y0 : 0;
+    a.gnx = win ? d->p.whole_nx : d->nx;
+    a.gny = win ? d->p.whole_ny : d->ny;
+    a.own_x0 = win ? d->p.own_x0 : 0;
+    a.own_x1 = win ? d->p.own_x1 : d->nx;
+    a.own_y0 = win ? d->p.own_y0 : 0;
+    a.own_y1 = win ? d->p.own_y1 : d->ny;
     return a;
 }
 
@@ -422,6 +433,20 @@ int validate(const swe_domain_desc *d, const swe_params *p) {
     if (p->kernel != 0 && p->kernel != 1) return SWE_ERR_INVALID_ARG;
     if (p->cfl_faces != 0 && p->cfl_faces != 1) return SWE_ERR_INVALID_ARG;
     if (p->cfl_faces && (d->precision == SWE_F64 || p->kernel != 0)) return SWE_ERR_UNSUPPORTED;
+    // a window of a larger domain: inside it, with its own cells inside the window
+    if (p->whole_nx == 0 && p->whole_ny == 0) {
+        if (p->window_x0 || p->window_y0 || p->own_x0 || p->own_x1 || p->own_y0 || p->own_y1)
+            return SWE_ERR_INVALID_ARG;
+    } else {
+        if (p->whole_nx < 1 || p->whole_ny < 1 || p->window_x0 < 0 || p->window_y0 < 0 ||
+            (long long)p->window_x0 + d->nx > p->whole_nx || (long long)p->window_y0 + d->ny > p->whole_ny ||
+            p->own_x0 < 0 || p->own_x0 >= p->own_x1 || p->own_x1 > d->nx ||
+            p->own_y0 < 0 || p->own_y0 >= p->own_y1 || p->own_y1 > d->ny)
+            return SWE_ERR_INVALID_ARG;
+        for (int e = 0; e < 4; e++)
+            if (d->bc[e] == SWE_BC_PERIODIC) return SWE_ERR_UNSUPPORTED;
+        if (d->precision == SWE_F64 || p->kernel != 0 || p->cfl_faces) return SWE_ERR_UNSUPPORTED;
+    }
     return SWE_OK;
 }
 
@@ -471,6 +496,8 @@ void swe_default_params(swe_params *p) {
     p->t0 = 0.0;
     p->kernel = 0;
     p->cfl_faces = 0;
+    p->window_x0 = p->window_y0 = p->whole_nx = p->whole_ny = 0;
+    p->own_x0 = p->own_x1 = p->own_y0 = p->own_y1 = 0;
 }
 
 int swe_create_domain(const swe_domain_desc *d, const swe_params *p, void *stream, swe_handle *out) {
@@ -529,7 +556,15 @@ int swe_set_forcing(swe_handle h, int kind, int n_frames, const double *times, c
 
 namespace {
 
+int split_step_check(swe_handle h, int n_steps);
+
 int step_check(swe_handle h, int n_steps) {
+    // a window's clock advances only with its sub-domains (swe_split_step)
+    if (h && h->p.whole_nx > 0) return SWE_ERR_UNSUPPORTED;
+    return split_step_check(h, n_steps);
+}
+
+int split_step_check(swe_handle h, int n_steps) {
     if (!h || n_steps < 0) return SWE_ERR_INVALID_ARG;
     if (h->sticky_numeric) return SWE_ERR_NUMERIC;
     if ((h->bc[0] == SWE_BC_NESTED || h->bc[1] == SWE_BC_NESTED || h->bc[2] == SWE_BC_NESTED ||
@@ -934,7 +969,7 @@ int swe_batch_create(void *stream, int max_domains, swe_batch_handle *out) {
 
 int swe_batch_add(swe_batch_handle b, swe_handle d) {
     if (!b || !d) return SWE_ERR_INVALID_ARG;
-    if (d->prec == SWE_F64 || !d->fast() || d->p.cfl_faces) return SWE_ERR_UNSUPPORTED;
+    if (d->prec == SWE_F64 || !d->fast() || d->p.cfl_faces || d->p.whole_nx > 0) return SWE_ERR_UNSUPPORTED;
     if ((int)b->doms.size() >= b->cap) return SWE_ERR_INVALID_ARG;
     for (swe_handle x : b->doms)
         if (x == d) return SWE_ERR_INVALID_ARG;
@@ -1040,6 +1075,162 @@ int swe_batch_destroy(swe_batch_handle b) {
     cudaFree(b->d_n); cudaFree(b->d_done); cudaFree(b->d_t); cudaFree(b->d_tile_dom);
     delete b;
     return e == cudaSuccess ? SWE_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// domain decomposition on one device
+
+namespace {
+
+struct Box { long long x0, x1, y0, y1; };
+
+Box own_box(const swe_domain *d) {
+    return {d->p.window_x0 + (long long)d->p.own_x0, d->p.window_x0 + (long long)d->p.own_x1,
+            d->p.window_y0 + (long long)d->p.own_y0, d->p.window_y0 + (long long)d->p.own_y1};
+}
+
+Box window_box(const swe_domain *d) {
+    return {d->p.window_x0, d->p.window_x0 + (long long)d->nx, d->p.window_y0, d->p.window_y0 + (long long)d->ny};
+}
+
+bool overlap(const Box &a, const Box &b, Box *out) {
+    Box o{std::max(a.x0, b.x0), std::min(a.x1, b.x1), std::max(a.y0, b.y0), std::min(a.y1, b.y1)};
+    if (o.x0 >= o.x1 || o.y0 >= o.y1) return false;
+    if (out) *out = o;
+    return true;
+}
+
+long long area(const Box &b) { return (b.x1 - b.x0) * (b.y1 - b.y0); }
+
+// The sub-domains form a decomposition: windows of one whole domain with
+// the same cell size, precision, stream and clock parameters, own cells
+// that tile the whole domain once, every halo cell owned by another one.
+int split_check(const swe_handle *doms, int n) {
+    if (!doms || n < 1 || n > swe::kSplitMax) return SWE_ERR_INVALID_ARG;
+    const swe_domain *a = doms[0];
+    for (int i = 0; i < n; i++) {
+        const swe_domain *d = doms[i];
+        if (!d || d->p.whole_nx <= 0 || !d->fast()) return SWE_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (doms[j] == d) return SWE_ERR_INVALID_ARG;
+        if (d->p.whole_nx != a->p.whole_nx || d->p.whole_ny != a->p.whole_ny || d->stream != a->stream ||
+            d->prec != a->prec || d->dx != a->dx || d->dy != a->dy || d->p.courant != a->p.courant ||
+            d->p.dt_fixed != a->p.dt_fixed || d->p.dt_update_every != a->p.dt_update_every)
+            return SWE_ERR_INVALID_ARG;
+    }
+    long long owned = 0;
+    for (int i = 0; i < n; i++) {
+        const Box oi = own_box(doms[i]);
+        owned += area(oi);
+        long long halo = 0;
+        for (int j = 0; j < n; j++) {
+            Box o;
+            if (j == i) continue;
+            if (overlap(oi, own_box(doms[j]), nullptr)) return SWE_ERR_INVALID_ARG;
+            if (overlap(window_box(doms[i]), own_box(doms[j]), &o)) halo += area(o);
+        }
+        if (halo != area(window_box(doms[i])) - area(oi)) return SWE_ERR_INVALID_ARG;
+    }
+    if (owned != (long long)a->p.whole_nx * a->p.whole_ny) return SWE_ERR_INVALID_ARG;
+    return SWE_OK;
+}
+
+swe::SplitClocks split_clocks(const swe_handle *doms, int n) {
+    swe::SplitClocks c;
+    memset(&c, 0, sizeof c);
+    c.n = n;
+    const StageArgs<float> a0 = make_args<float>(doms[0]);
+    c.clk = a0.clk;
+    for (int k = 0; k < n; k++) {
+        const StageArgs<float> a = make_args<float>(doms[k]);
+        c.ctl[k] = a.ctl;
+        c.bnd[k] = a.bnd;
+        c.wind[k] = a.wind;
+    }
+    return c;
+}
+
+// Every (sub-domain, owner) pair whose window and own cells overlap, in
+// launches of at most kHaloCopies copies.
+int split_exchange(const swe_handle *doms, int n, int what, cudaStream_t st, long long *launches) {
+    swe::HaloTable t;
+    memset(&t, 0, sizeof t);
+    for (int k = 0; k < n; k++) {
+        const swe_domain *d = doms[k];
+        swe::SplitPlanes &P = t.dom[k];
+        for (int v = 0; v < 3; v++) {
+            P.q[0][v] = (float *)d->q[0][v];
+            P.q[1][v] = (float *)d->q[1][v];
+            P.d1[v] = (float *)d->d1[v];
+        }
+        P.ctl = d->ctl;
+        P.pitch = d->pitch;
+        P.wx0 = d->p.window_x0;
+        P.wy0 = d->p.window_y0;
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            Box o;
+            if (i == j || !overlap(window_box(doms[i]), own_box(doms[j]), &o)) continue;
+            t.copy[t.n_copies++] = swe::HaloCopy{i, j, (int)o.x0, (int)o.x1, (int)o.y0, (int)o.y1};
+            if (t.n_copies == swe::kHaloCopies) {
+                cudaError_t e = swe::launch_halo_copy(t, what, st);
+                if (e != cudaSuccess) return cuda_fail(e);
+                ++*launches;
+                t.n_copies = 0;
+            }
+        }
+    if (t.n_copies > 0) {
+        cudaError_t e = swe::launch_halo_copy(t, what, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        ++*launches;
+    }
+    return SWE_OK;
+}
+
+}  // namespace
+
+int swe_split_sync(const swe_handle *doms, int n) {
+    swe::TraceRange trace("swe_split_sync");
+    int rc = split_check(doms, n);
+    if (rc) return rc;
+    cudaStream_t st = doms[0]->stream;
+    for (int k = 0; k < n; k++) {
+        cudaError_t e = swe::launch_speed(make_args<float>(doms[k]), st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    cudaError_t e = swe::launch_split_clock(split_clocks(doms, n), 0, st);
+    for (int k = 0; k < n && e == cudaSuccess; k++) e = swe::launch_edge_fill(make_args<float>(doms[k]), st);
+    return e == cudaSuccess ? SWE_OK : cuda_fail(e);
+}
+
+int swe_split_step(const swe_handle *doms, int n, int n_steps) {
+    swe::TraceRange trace("swe_split_step");
+    int rc = split_check(doms, n);
+    if (rc) return rc;
+    for (int k = 0; k < n; k++)
+        if ((rc = split_step_check(doms[k], n_steps))) return rc;
+    cudaStream_t st = doms[0]->stream;
+    const swe::SplitClocks clocks = split_clocks(doms, n);
+    long long launches = 0;
+    for (int s = 0; s < n_steps; s++) {
+        for (int k = 0; k < n; k++) {
+            cudaError_t e = swe::launch_domain_stage(doms[k]->one, 1, st);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        if ((rc = split_exchange(doms, n, 1, st, &launches))) return rc;
+        for (int k = 0; k < n; k++) {
+            cudaError_t e = swe::launch_domain_stage(doms[k]->one, 2, st);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        cudaError_t e = swe::launch_split_clock(clocks, 1, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if ((rc = split_exchange(doms, n, 0, st, &launches))) return rc;
+        for (int k = 0; k < n; k++) doms[k]->launches += 2;
+        doms[0]->launches += 1;
+    }
+    doms[0]->launches += launches;
+    return SWE_OK;
 }
 
 }  // extern "C"

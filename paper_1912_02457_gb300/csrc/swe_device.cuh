@@ -218,7 +218,9 @@ template <typename T>
 __device__ T bnd_value(const StageArgs<T> &a, int e, int r, int v, int k, int stage) {
     const ForcingDev &F = a.bnd;
     int nb = e < 2 ? F.n1 : F.n2;
-    int n = e < 2 ? a.nx : a.ny;
+    // a window samples the edge at the whole domain's positions
+    int n = e < 2 ? a.gnx : a.gny;
+    k += e < 2 ? a.off_x : a.off_y;
     long long off = (e >= 1 ? 6LL * F.n1 : 0) + (e >= 2 ? 6LL * F.n1 : 0) + (e >= 3 ? 6LL * F.n2 : 0);
     int k0, k1;
     double w;
@@ -278,18 +280,19 @@ __device__ __forceinline__ void wind_at(const StageArgs<T> &a, int i, int j, int
     }
     const ForcingDev &F = a.wind;
     // sampling positions and weights in the domain's precision (an FP64
-    // domain interpolates in FP64, like its nesting frames)
+    // domain interpolates in FP64, like its nesting frames); a window
+    // samples at the whole domain's positions
     int x0, x1, y0, y1;
     T wx, wy;
     if constexpr (sizeof(T) == sizeof(double)) {
         double px, py;
-        axis_pos(i, a.nx, F.n1, x0, x1, px);
-        axis_pos(j, a.ny, F.n2, y0, y1, py);
+        axis_pos(i + a.off_x, a.gnx, F.n1, x0, x1, px);
+        axis_pos(j + a.off_y, a.gny, F.n2, y0, y1, py);
         wx = T(px); wy = T(py);
     } else {
         float px, py;
-        axis_pos_f(i, a.nx, F.n1, x0, x1, px);
-        axis_pos_f(j, a.ny, F.n2, y0, y1, py);
+        axis_pos_f(i + a.off_x, a.gnx, F.n1, x0, x1, px);
+        axis_pos_f(j + a.off_y, a.gny, F.n2, y0, y1, py);
         wx = T(px); wy = T(py);
     }
     int fk = a.ctl->wk[stage];

@@ -48,6 +48,7 @@ struct ClockParams {
     double rho_ratio;         // rho_air / rho_water
     int fp32;                 // an FP32 domain: frame weights and wind stress in FP32
     int cfl_faces;            // dt from the faces' one-sided speeds (a speed pass per step)
+    int split;                // a sub-domain: stage 2 leaves its CFL maximum for a shared clock
 };
 
 struct ForcingDev {
@@ -90,6 +91,13 @@ struct StageArgs {
     int n_items;
     // elements of each buffer (checked by the bounds-checked debug builds)
     long long n_plane, n_corner, n_edge, n_bnd, n_wind;
+    // a window of a larger domain: cell (0, 0) is the whole domain's cell
+    // (off_x, off_y), which has gnx x gny cells (forcing is sampled at the
+    // whole domain's positions); the CFL maximum and the error report cover
+    // the own cells [own_x0, own_x1) x [own_y0, own_y1). A whole domain:
+    // offsets 0, gnx = nx, gny = ny, every cell its own.
+    int off_x, off_y, gnx, gny;
+    int own_x0, own_x1, own_y0, own_y1;
 };
 
 // A single FP32 domain handed to the stage kernel with the launch (kernel

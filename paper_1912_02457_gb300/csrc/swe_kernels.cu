@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(256) speed_kernel(StageArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     T speed = T(0);
-    if (i < a.nx && j < a.ny) {
+    // the domain's own cells (all of them unless it is a window)
+    if (i >= a.own_x0 && i < a.own_x1 && j >= a.own_y0 && j < a.own_y1) {
         const long long cp = a.cpitch;
         const T *H = a.H + (long long)j * cp + i;
         T c00 = H[0], c10 = H[1], c01 = H[cp], c11 = H[cp + 1];
@@ -255,6 +256,49 @@ __global__ void clock_kernel(StepCtl *ctl, ClockParams clk, ForcingDev bnd, Forc
     ctl->speed32 = 0u;
     ctl->speed64 = 0ull;
     clock_update(ctl, clk, bnd, wind, speed, mode);
+}
+
+// One clock evaluation for the sub-domains of a decomposed domain, from
+// the largest of their CFL maxima (each FP32 sub-domain's stage 2 or speed
+// pass left its own in speed32; the maximum is taken over the bit patterns
+// of these non-negative floats, as the atomics of a whole domain take it):
+// every clock advances with the same speed, so to the same t, dt and
+// forcing brackets.
+__global__ void split_clock_kernel(SplitClocks c, int mode) {
+    __shared__ unsigned int bits;
+    if (threadIdx.x == 0) {
+        unsigned int m = 0u;
+        for (int k = 0; k < c.n; k++) m = max(m, c.ctl[k]->speed32);
+        bits = m;
+    }
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k >= c.n) return;
+    StepCtl *ctl = c.ctl[k];
+    if (mode == 1 && ctl->done) return;
+    ctl->speed32 = 0u;
+    ctl->speed64 = 0ull;
+    clock_update(ctl, c.clk, c.bnd[k], c.wind[k], (double)__uint_as_float(bits), mode);
+}
+
+// The halo exchange of a decomposed domain: copy c of the table moves the
+// cells of a box (whole-domain coordinates) from the sub-domain that owns
+// them into another's window; what = 0: the current state (each
+// sub-domain's buffer chosen by its device-side parity), 1: the stage-1
+// increment.
+__global__ void __launch_bounds__(256) halo_copy_kernel(HaloTable t, int what) {
+    const HaloCopy c = t.copy[blockIdx.y];
+    const SplitPlanes &D = t.dom[c.dst], &S = t.dom[c.src];
+    const int w = c.x1 - c.x0, n = w * (c.y1 - c.y0);
+    const int dp = what == 0 ? D.ctl->parity : 0, sp = what == 0 ? S.ctl->parity : 0;
+    float *const *dst = what == 0 ? D.q[dp] : D.d1;
+    const float *const *src = what == 0 ? S.q[sp] : S.d1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int x = c.x0 + k % w, y = c.y0 + k / w;
+        const long long so = (long long)(y - S.wy0) * S.pitch + (x - S.wx0);
+        const long long dof = (long long)(y - D.wy0) * D.pitch + (x - D.wx0);
+        for (int v = 0; v < 3; v++) dst[v][dof] = src[v][so];
+    }
 }
 
 __global__ void set_clock_kernel(StepCtl *ctl, double t, double dt, long long step) {
@@ -390,6 +434,26 @@ cudaError_t launch_init_clock(const StageArgs<T> &a, cudaStream_t st, double t, 
         speed_kernel<T><<<ref_grid(a.nx, a.ny), ref_block(), 0, st>>>(a);
         clock_kernel<T><<<1, 1, 0, st>>>(a.ctl, a.clk, a.bnd, a.wind, 0);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_speed(const StageArgs<float> &a, cudaStream_t st) {
+    speed_kernel<float><<<ref_grid(a.nx, a.ny), ref_block(), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_clock(const SplitClocks &c, int mode, cudaStream_t st) {
+    split_clock_kernel<<<1, 32, 0, st>>>(c, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_copy(const HaloTable &t, int what, cudaStream_t st) {
+    if (t.n_copies <= 0) return cudaSuccess;
+    int most = 0;
+    for (int k = 0; k < t.n_copies; k++)
+        most = std::max(most, (t.copy[k].x1 - t.copy[k].x0) * (t.copy[k].y1 - t.copy[k].y0));
+    const int blocks = std::min(64, std::max(1, (most + 255) / 256));
+    halo_copy_kernel<<<dim3(blocks, t.n_copies), 256, 0, st>>>(t, what);
     return cudaGetLastError();
 }
 

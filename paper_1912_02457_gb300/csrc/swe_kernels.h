@@ -54,6 +54,40 @@ cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st
 // or the forcing was set); stage 1 of every step fills the next level.
 cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st);
 long long edge_floats(int nx, int ny);   // both time levels
+
+// Domain decomposition on one device (swe_kernels.cu): the largest CFL
+// maximum of the own cells of every sub-domain (launch_speed, once per
+// sub-domain, at set-up), one clock evaluation for all of them
+// (launch_split_clock; mode as in clock_advance), and the halo exchange
+// between their planes (launch_halo_copy; what 0: the current state, 1:
+// the stage-1 increment).
+constexpr int kSplitMax = 16;            // SWE_SPLIT_MAX
+constexpr int kHaloCopies = 48;          // copies per launch
+struct SplitClocks {
+    int n;
+    StepCtl *ctl[kSplitMax];
+    ClockParams clk;
+    ForcingDev bnd[kSplitMax], wind[kSplitMax];
+};
+struct SplitPlanes {
+    float *q[2][3];
+    float *d1[3];
+    const StepCtl *ctl;
+    long long pitch;
+    int wx0, wy0;                        // window origin in the whole domain
+};
+struct HaloCopy {
+    int dst, src;                        // sub-domain indices
+    int x0, x1, y0, y1;                  // box in whole-domain cells
+};
+struct HaloTable {
+    int n_copies;
+    SplitPlanes dom[kSplitMax];
+    HaloCopy copy[kHaloCopies];
+};
+cudaError_t launch_speed(const StageArgs<float> &a, cudaStream_t st);
+cudaError_t launch_split_clock(const SplitClocks &c, int mode, cudaStream_t st);
+cudaError_t launch_halo_copy(const HaloTable &t, int what, cudaStream_t st);
 int diag_blocks(int nx, int ny);
 
 // Record e for swe_last_cuda_error and return SWE_ERR_CUDA (swe_capi.cu).

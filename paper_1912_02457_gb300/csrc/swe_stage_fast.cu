@@ -64,11 +64,12 @@ __device__ __forceinline__ void bnd_state_f(const StageArgs<float> &a, int e, in
                                             int stage, float &v0, float &v1, float &v2) {
     const ForcingDev &F = a.bnd;
     int nb = e < 2 ? F.n1 : F.n2;
-    int n = e < 2 ? a.nx : a.ny;
+    // a window samples the edge at the whole domain's positions
+    int n = e < 2 ? a.gnx : a.gny;
     long long off = (e >= 1 ? 6LL * F.n1 : 0) + (e >= 2 ? 6LL * F.n1 : 0) + (e >= 3 ? 6LL * F.n2 : 0);
     int k0, k1;
     float w;
-    bnd_pos_f(k, n, nb, k0, k1, w);
+    bnd_pos_f(k + (e < 2 ? a.off_x : a.off_y), n, nb, k0, k1, w);
     int fk = a.ctl->bk[stage];
     float s = a.ctl->bs_f[stage];
     long long fs = 12LL * (F.n1 + F.n2);
@@ -282,6 +283,8 @@ __device__ __forceinline__ Face<float> shfl_dn_face(const Face<float> &F) {
 __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nblocks, int mode) {
     if (threadIdx.x != 0) return;
     atomicMax(&a.ctl->speed32, __float_as_uint(block_speed));
+    // a sub-domain leaves its maximum for the clock of all sub-domains
+    if (mode == 5) return;
     __threadfence();                           // the block's maximum lands before its count
     // every block loads the clock's inputs while its count is in flight;
     // the last one then needs no further round trip to memory
@@ -302,7 +305,7 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nb
 // Per-warp constants of one strip.
 struct StripCtx {
     int lane, i, j0, j1, par;
-    bool out_lane, frs_tile, wind_on, wind_uni;
+    bool out_lane, own_col, frs_tile, wind_on, wind_uni;
     float dt, taux, tauy, rho_ratio;
 };
 
@@ -486,8 +489,12 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
             }
             a.q[par ^ 1][0][s] = q0; a.q[par ^ 1][1][s] = q1; a.q[par ^ 1][2][s] = q2;
             if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
-            if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + k.i);
-            w.speed = fmaxf(w.speed, cell_speed(a, q0, q1, q2, w.A.Hbar));
+            // the CFL maximum and the error report cover the domain's own
+            // cells (all of them unless it is a window of a larger domain)
+            if (k.own_col && (unsigned)(ro - a.own_y0) < (unsigned)(a.own_y1 - a.own_y0)) {
+                if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + k.i);
+                w.speed = fmaxf(w.speed, cell_speed(a, q0, q1, q2, w.A.Hbar));
+            }
         }
     }
 
@@ -552,6 +559,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         edge_fill(a, k.par ^ 1, 1, b * (kWarps * 32) + threadIdx.x, nblocks * (kWarps * 32));
     }
     k.out_lane = lane >= 2 && lane < 2 + kStrip && k.i < a.nx;
+    k.own_col = (unsigned)(k.i - a.own_x0) < (unsigned)(a.own_x1 - a.own_x0);
     k.dt = (float)dt;
     k.rho_ratio = (float)a.clk.rho_ratio;
     k.wind_on = a.wind.n > 0;
@@ -620,7 +628,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         float bs = 0.f;
         if (threadIdx.x == 0)
             for (int q = 0; q < kWarps; q++) bs = fmaxf(bs, sh[q]);
-        finish_step(a, bs, nblocks, STAGE == 0 ? 3 : (a.clk.cfl_faces ? 4 : 1));
+        finish_step(a, bs, nblocks, STAGE == 0 ? 3 : a.clk.split ? 5 : (a.clk.cfl_faces ? 4 : 1));
     }
 }
 

@@ -39,7 +39,10 @@ class Params(C.Structure):
                 ("frs_width", C.c_int), ("dt_update_every", C.c_int),
                 ("dt_fixed", C.c_double), ("rho_air", C.c_double),
                 ("rho_water", C.c_double), ("t0", C.c_double), ("kernel", C.c_int),
-                ("cfl_faces", C.c_int)]
+                ("cfl_faces", C.c_int),
+                ("window_x0", C.c_int), ("window_y0", C.c_int), ("whole_nx", C.c_int),
+                ("whole_ny", C.c_int), ("own_x0", C.c_int), ("own_x1", C.c_int),
+                ("own_y0", C.c_int), ("own_y1", C.c_int)]
 
 
 class DomainDesc(C.Structure):
@@ -97,6 +100,8 @@ SIGNATURES = {
     "swe_batch_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "swe_batch_launches": (C.c_longlong, [C.c_void_p]),
     "swe_batch_destroy": (C.c_int, [C.c_void_p]),
+    "swe_split_sync": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "swe_split_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "swe_diagnostics_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_int, C.c_int, C.c_longlong, C.c_longlong,
                                           C.c_double, C.c_double, C.c_double, C.c_double,
@@ -253,7 +258,11 @@ class Domain:
     'f32', 'f32_kahan', 'f64'; ``stream`` a cudaStream_t as an int (0: the
     legacy default stream, which is also PyTorch's default stream)."""
 
-    def __init__(self, wl, precision: str = "f32", stream: int = 0, kernel: str = "fast"):
+    def __init__(self, wl, precision: str = "f32", stream: int = 0, kernel: str = "fast",
+                 window=None):
+        """``window``: (part, whole_nx, whole_ny) with ``part`` an entry of
+        ``synth.partition``: ``wl`` is that window of a larger domain (see
+        swe_params in swe.h), stepped with its sub-domains by ``split``."""
         L = load()
         self.wl = wl
         self.prec = PRECISIONS[precision]
@@ -277,6 +286,12 @@ class Domain:
         d.f_const, d.theta_const = wl.f_const, wl.theta_const
         d.src_is_device = 0
         p = params_from(wl.params, wl.t0, {"fast": 0, "reference": 1}[kernel])
+        if window is not None:
+            part, p.whole_nx, p.whole_ny = window
+            wx0, _, wy0, _ = part["win"]
+            x0, x1, y0, y1 = part["own"]
+            p.window_x0, p.window_y0 = wx0, wy0
+            p.own_x0, p.own_x1, p.own_y0, p.own_y1 = x0 - wx0, x1 - wx0, y0 - wy0, y1 - wy0
         h = C.c_void_p()
         _check(L.swe_create_domain(C.byref(d), C.byref(p), C.c_void_p(stream), C.byref(h)),
                "swe_create_domain")

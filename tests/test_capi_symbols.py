@@ -46,7 +46,7 @@ def test_binding_covers_every_symbol(built_lib):
     from paper_1912_02457_gb300 import swe
     L = swe.load(built_lib)
     assert set(swe.SIGNATURES) == declared_functions()
-    assert L.swe_abi_version() == 1
+    assert L.swe_abi_version() == 2
     assert L.swe_status_string(-4) == b"non-finite state or time step"
     p = swe.default_params()
     assert p.g == 9.81 and p.theta_mm == 1.3 and p.frs_width == 10
