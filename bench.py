@@ -518,6 +518,34 @@ def run_rossby(args):
                       "unit": UNIT, "precision": args.precision, "results": out}), flush=True)
 
 
+def run_split(args):
+    """The coastal 4096^2 domain stepped whole and as 2x2 and 4x4 windows
+    exchanging halos on this one GPU (swe_split_step): cell-updates/s of
+    the whole domain either way, i.e. the cost of the decomposition's extra
+    launches, halo cells and copies on one device (not a scaling figure)."""
+    import torch
+    from paper_1912_02457_gb300 import build, swe, synth
+    from paper_1912_02457_gb300.split import SplitDomain
+    build.build()
+    swe.load()
+    stream = torch.cuda.Stream()
+    wl = synth.coastal(4096, 4096, dtype=np.float32)
+    out = []
+    with swe.Domain(wl, args.precision, stream=stream.cuda_stream) as d:
+        d.step(args.warmup)
+        el = _timed_steps(torch, d, args.steps, stream)
+        out.append({"split": "whole", "steps": args.steps,
+                    "cell_updates_per_s": float(wl.nx * wl.ny * args.steps / el)})
+    for px, py in ((2, 2), (4, 4)):
+        with SplitDomain(wl, px, py, args.precision, stream=stream.cuda_stream) as s:
+            s.step(args.warmup)
+            el = _timed_steps(torch, s, args.steps, stream)
+            out.append({"split": f"{px}x{py}", "steps": args.steps,
+                        "cell_updates_per_s": float(wl.nx * wl.ny * args.steps / el)})
+    print(json.dumps({"metric": METRIC, "workload": "coastal 4096x4096, whole and split into windows on one GPU",
+                      "unit": UNIT, "precision": args.precision, "results": out}), flush=True)
+
+
 def run_ensemble(args):
     """64 domains of uneven sizes in one batch: one launch per
     stage (graph-captured, autotuned tiles) against launching the same
@@ -703,7 +731,8 @@ def main():
                     help="time step from the cell averages (the scheme's reading) or the faces' speeds")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep", "rossby"),
+    ap.add_argument("--workload", choices=("coastal1024", "sweep", "ensemble", "serve", "prep", "rossby",
+                                           "split"),
                     default="coastal1024")
     ap.add_argument("--domains", type=int, default=64)
     ap.add_argument("--requests", type=int, default=32)
@@ -725,6 +754,8 @@ def main():
         return run_serve(args)
     if args.workload == "prep":
         return run_prep(args)
+    if args.workload == "split":
+        return run_split(args)
     if args.workload == "rossby":
         return run_rossby(args)
     return run_ours(args)

@@ -232,6 +232,18 @@ int ensure_wet(swe_domain *d) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     d->dfree(dev);
     if (e != cudaSuccess) { d->wet.clear(); return cuda_fail(e); }
+    if (d->p.whole_nx > 0) {
+        // a window plans its own rows only, and no strip without an own
+        // column: those cells are never written, the halo exchange fills
+        // them (the halo columns of the strips it does march are written
+        // and overwritten, and left out of its CFL maximum)
+        const int strips = swe::fast_strips(d->nx), S = swe::kStripColumns;
+        for (int st = 0; st < strips; st++) {
+            const bool cols = st * S < d->p.own_x1 && st * S + S > d->p.own_x0;
+            for (int j = 0; j < d->ny; j++)
+                if (!cols || j < d->p.own_y0 || j >= d->p.own_y1) d->wet[(size_t)st * d->ny + j] = 0;
+        }
+    }
     return SWE_OK;
 }
 

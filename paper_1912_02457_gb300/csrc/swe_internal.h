@@ -93,9 +93,9 @@ struct StageArgs {
     long long n_plane, n_corner, n_edge, n_bnd, n_wind;
     // a window of a larger domain: cell (0, 0) is the whole domain's cell
     // (off_x, off_y), which has gnx x gny cells (forcing is sampled at the
-    // whole domain's positions); the CFL maximum and the error report cover
-    // the own cells [own_x0, own_x1) x [own_y0, own_y1). A whole domain:
-    // offsets 0, gnx = nx, gny = ny, every cell its own.
+    // whole domain's positions); the CFL maximum covers the own cells
+    // [own_x0, own_x1) x [own_y0, own_y1). A whole domain: offsets 0,
+    // gnx = nx, gny = ny, every cell its own.
     int off_x, off_y, gnx, gny;
     int own_x0, own_x1, own_y0, own_y1;
 };

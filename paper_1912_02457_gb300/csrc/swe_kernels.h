@@ -39,6 +39,7 @@ const char *fast_part_name(int part, bool faces);
 // kPlanUnit per plain row. wet: strips x ny flags of launch_wet_strips
 // (strip-major) on the host, or NULL (every cell wet).
 constexpr int kPlanUnit = 100;
+constexpr int kStripColumns = 28;        // output columns of a warp item
 int fast_strips(int nx);
 int fast_budget(int nx, int ny, const unsigned char *wet, const int bc[4], int frs_width);
 // alone: the plan of a domain launched by itself (a batch launches many)

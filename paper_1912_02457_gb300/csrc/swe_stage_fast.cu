@@ -34,7 +34,7 @@ namespace swe {
 
 namespace {
 
-constexpr int kStrip = 28;           // output columns per warp
+constexpr int kStrip = kStripColumns;   // output columns per warp (28)
 constexpr int kWarps = 4;            // warps per block
 #ifndef SWE_MIN_BLOCKS
 #define SWE_MIN_BLOCKS 4             // resident blocks per SM the register budget targets
@@ -305,7 +305,7 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nb
 // Per-warp constants of one strip.
 struct StripCtx {
     int lane, i, j0, j1, par;
-    bool out_lane, own_col, frs_tile, wind_on, wind_uni;
+    bool out_lane, frs_tile, wind_on, wind_uni;
     float dt, taux, tauy, rho_ratio;
 };
 
@@ -489,12 +489,8 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
             }
             a.q[par ^ 1][0][s] = q0; a.q[par ^ 1][1][s] = q1; a.q[par ^ 1][2][s] = q2;
             if (KAHAN) { a.comp[0][s] = c0; a.comp[1][s] = c1; a.comp[2][s] = c2; }
-            // the CFL maximum and the error report cover the domain's own
-            // cells (all of them unless it is a window of a larger domain)
-            if (k.own_col && (unsigned)(ro - a.own_y0) < (unsigned)(a.own_y1 - a.own_y0)) {
-                if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + k.i);
-                w.speed = fmaxf(w.speed, cell_speed(a, q0, q1, q2, w.A.Hbar));
-            }
+            if (!(isfinite(q0) && isfinite(q1) && isfinite(q2))) flag_error(a.ctl, ro * a.nx + k.i);
+            w.speed = fmaxf(w.speed, cell_speed(a, q0, q1, q2, w.A.Hbar));
         }
     }
 
@@ -559,7 +555,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         edge_fill(a, k.par ^ 1, 1, b * (kWarps * 32) + threadIdx.x, nblocks * (kWarps * 32));
     }
     k.out_lane = lane >= 2 && lane < 2 + kStrip && k.i < a.nx;
-    k.own_col = (unsigned)(k.i - a.own_x0) < (unsigned)(a.own_x1 - a.own_x0);
     k.dt = (float)dt;
     k.rho_ratio = (float)a.clk.rho_ratio;
     k.wind_on = a.wind.n > 0;
@@ -621,7 +616,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
         // averages); the speed pass: the largest face speed over the cell
         // size (eq:cfl with the faces' one-sided speeds)
         __shared__ float sh[kWarps];
-        float speed = STAGE == 0 ? fmaxf(w.fx * a.inv_dx, w.fy * a.inv_dy) : w.speed;
+        // a window of a larger domain takes the maximum over its own cells:
+        // its halo rows are not in its plan, and the lanes of its halo
+        // columns (written, then overwritten by the halo exchange) drop out
+        // here, once, rather than in every row
+        const bool own_col = (unsigned)(k.i - a.own_x0) < (unsigned)(a.own_x1 - a.own_x0);
+        float speed = STAGE == 0 ? fmaxf(w.fx * a.inv_dx, w.fy * a.inv_dy) : (own_col ? w.speed : 0.f);
         for (int o = 16; o > 0; o >>= 1) speed = fmaxf(speed, __shfl_xor_sync(0xffffffffu, speed, o));
         if (lane == 0) sh[warp] = speed;
         __syncthreads();
