@@ -810,6 +810,7 @@ struct swe_batch {
     int *d_done = nullptr;
     double *d_t = nullptr;
     int blocks = 0;
+    bool gridded = false;           // some domain has gridded wind (which stage kernel)
     cudaGraphExec_t graph = nullptr;
     static constexpr int kGraphSteps = 8;
     long long launches = 0;
@@ -852,9 +853,13 @@ int batch_upload_impl(swe_batch *b) {
     }
     CK(cudaMemcpy(b->d_tile_start, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_n, &n, sizeof(int), cudaMemcpyHostToDevice));
-    // one block per tile: a new tile count (or table) needs a new graph
+    // one block per tile: a new tile count (or table) needs a new graph,
+    // and so does a change of the stage kernel (gridded wind or not)
     const int blocks = start[n] > 0 ? start[n] : 1;
-    bool regraph = blocks != b->blocks;
+    bool gridded = false;
+    for (int k = 0; k < n; k++) gridded |= args[k].wind.n > 0 && !args[k].clk.wind_uniform;
+    bool regraph = blocks != b->blocks || gridded != b->gridded;
+    b->gridded = gridded;
     if (start[n] > b->tile_dom_cap) {
         int *p = nullptr;
         CK(cudaMalloc(&p, sizeof(int) * (size_t)start[n]));
@@ -890,7 +895,7 @@ swe::BatchTable batch_table(const swe_batch *b) {
 
 int batch_launch_step(swe_batch *b, cudaStream_t st) {
     for (int stage = 1; stage <= 2; stage++) {
-        cudaError_t e = swe::launch_batch_stage(batch_table(b), b->blocks, stage, st);
+        cudaError_t e = swe::launch_batch_stage(batch_table(b), b->blocks, stage, b->gridded, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return SWE_OK;

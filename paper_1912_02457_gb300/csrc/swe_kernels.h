@@ -48,7 +48,9 @@ void fast_plan(int nx, int ny, const unsigned char *wet, const int bc[4], int fr
 int fast_tiles(int n_items);
 cudaError_t launch_wet_strips(const float *H, long long cpitch, int nx, int ny, unsigned char *out,
                               cudaStream_t st);
-cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st);
+// gridded: some domain of the batch has gridded wind (the kernel with the
+// per-cell wind sampling); a single domain's launch decides by its own wind.
+cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, bool gridded, cudaStream_t st);
 // The same kernel for one domain whose arguments travel with the launch.
 cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st);
 // Fill the external edge state of the current time level (after the clock

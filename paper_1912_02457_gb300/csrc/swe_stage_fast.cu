@@ -305,7 +305,7 @@ __device__ void finish_step(const StageArgs<float> &a, float block_speed, int nb
 // Per-warp constants of one strip.
 struct StripCtx {
     int lane, i, j0, j1, par;
-    bool out_lane, frs_tile, wind_on, wind_uni;
+    bool out_lane, frs_tile, wind_on;
     float dt, taux, tauy, rho_ratio;
 };
 
@@ -323,11 +323,15 @@ struct Window {
 // One row of the march: the x-part of row r (X), the y-reconstruction of
 // row r-1 (Y) and the flux across its south face (G), and the update of row
 // r-2 (OUT); the flags are warp-uniform. This body is instantiated once per
-// kernel on purpose: every cell then runs the same machine code wherever it
-// sits in a strip, so results do not depend on the tiling (bit for bit,
-// which the batch tests check). Land cells compute harmless values that
-// selects discard.
-template <int STAGE>
+// kernel and wind kind on purpose: every cell of a domain then runs the same
+// machine code wherever it sits in a strip, alone, in a batch or in a
+// window, so results do not depend on the tiling (bit for bit, which the
+// batch and split tests check). Land cells compute harmless values that
+// selects discard. GW: the domain's wind is a grid sampled per cell (else
+// uniform or none); uniform-wind domains carry no code of the gridded path
+// in their march (with it, the coastal 1024^2 step measured 1.5% slower
+// although that branch is never taken).
+template <int STAGE, bool GW>
 __device__ __forceinline__ void march_row(const StageArgs<float> &a, const StripCtx &k, int r,
                                           const Cell<float> &c, Window &w, const bool KAHAN,
                                           const bool X, const bool Y, const bool G, const bool OUT) {
@@ -393,7 +397,7 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
         acc0[1] += c.f * c.hv;
         acc0[2] -= c.f * c.hu;
         if (k.wind_on) {
-            if (k.wind_uni) {
+            if (!GW) {
                 acc0[1] += k.taux;
                 acc0[2] += k.tauy;
             } else {
@@ -509,7 +513,7 @@ __device__ __forceinline__ void march_row(const StageArgs<float> &a, const Strip
 // the right edge and lets the tile height be chosen to fill whole waves.
 // `nblocks`: blocks of this domain in this launch (the last of them to
 // finish stage 2 advances the domain's clock).
-template <int STAGE>
+template <int STAGE, bool GW>
 __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, int rows, int strips,
                                            int nblocks, const bool KAHAN) {
     const int lane = threadIdx.x & 31;
@@ -558,7 +562,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
     k.dt = (float)dt;
     k.rho_ratio = (float)a.clk.rho_ratio;
     k.wind_on = a.wind.n > 0;
-    k.wind_uni = a.clk.wind_uniform != 0;
     k.taux = taux;
     k.tauy = tauy;
     // does any cell of this warp's strip lie in a flow-relaxation zone?
@@ -590,7 +593,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
             fetch_cell<STAGE>(a, par, i, r + 1, interior, nxt, &cur);
             Cell<float> c;
             decode_cell<STAGE>(a, i, r, cur, c);
-            march_row<STAGE>(a, k, r, c, w, KAHAN, false, false, false, false);
+            march_row<STAGE, GW>(a, k, r, c, w, KAHAN, false, false, false, false);
             cur = nxt;
         }
         // then each row runs its x part, the y part of the row below, the
@@ -605,7 +608,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
             if (r <= j1) fetch_cell<STAGE>(a, par, i, r + 1, interior, nxt, &cur);
             Cell<float> c;
             decode_cell<STAGE>(a, i, r, cur, c);
-            march_row<STAGE>(a, k, r, c, w, KAHAN, STAGE == 2 || r < j1, true, STAGE == 2 || r >= j0 + 1,
+            march_row<STAGE, GW>(a, k, r, c, w, KAHAN, STAGE == 2 || r < j1, true, STAGE == 2 || r >= j0 + 1,
                              STAGE != 0 && r >= j0 + 2);
             cur = nxt;
         }
@@ -643,8 +646,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<float> &a, int blk, i
 // kernel's parameter space, so a launch does not start with a chain of
 // table lookups in global memory. Either way the tile work below is the one
 // call site of stage_tile, so a domain computes the same bits alone or in
-// a batch.
-template <int STAGE>
+// a batch. GW: the kernel for domains with gridded wind (a batch with any
+// such domain launches it for all of them; uniform-wind domains alone and
+// in uniform batches launch the other).
+template <int STAGE, bool GW>
 __global__ void __launch_bounds__(kWarps * 32, SWE_MIN_BLOCKS)
 stage_batch_kernel(const BatchTable tab, const __grid_constant__ OneDomain one) {
     // the domain's arguments, staged once per block in shared memory (they
@@ -674,7 +679,7 @@ stage_batch_kernel(const BatchTable tab, const __grid_constant__ OneDomain one) 
             __syncthreads();
             have = d;
         }
-        stage_tile<STAGE>(sa, t - first, rows, strips, ntiles, sa.comp[0] != nullptr);
+        stage_tile<STAGE, GW>(sa, t - first, rows, strips, ntiles, sa.comp[0] != nullptr);
         __syncthreads();                        // shared scratch reused by the next tile
     }
 }
@@ -688,7 +693,7 @@ static int warp_slots() {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<2>, kWarps * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<2, false>, kWarps * 32, 0);
         slots = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4) * kWarps;
     }
     return slots;
@@ -940,7 +945,7 @@ cudaError_t launch_edge_fill(const StageArgs<float> &a, cudaStream_t st) {
 // (back-to-back steps 2.2% faster on the coastal 1024^2 step). After any
 // other stream work a launch is ordered as usual.
 static cudaError_t launch_stage(int stage, int blocks, const BatchTable &tab, const OneDomain &one,
-                                cudaStream_t st) {
+                                bool gridded, cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof cfg);
     cfg.gridDim = dim3(blocks);
@@ -951,22 +956,24 @@ static cudaError_t launch_stage(int stage, int blocks, const BatchTable &tab, co
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = stage == 0   ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<0>, tab, one)
-                    : stage == 1 ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<1>, tab, one)
-                                 : cudaLaunchKernelEx(&cfg, stage_batch_kernel<2>, tab, one);
+    cudaError_t e = stage == 0 ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<0, false>, tab, one)
+                    : stage == 1 ? (gridded ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<1, true>, tab, one)
+                                            : cudaLaunchKernelEx(&cfg, stage_batch_kernel<1, false>, tab, one))
+                                 : (gridded ? cudaLaunchKernelEx(&cfg, stage_batch_kernel<2, true>, tab, one)
+                                            : cudaLaunchKernelEx(&cfg, stage_batch_kernel<2, false>, tab, one));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, cudaStream_t st) {
+cudaError_t launch_batch_stage(const BatchTable &tab, int blocks, int stage, bool gridded, cudaStream_t st) {
     OneDomain none;
     memset(&none, 0, sizeof none);
-    return launch_stage(stage, blocks, tab, none, st);
+    return launch_stage(stage, blocks, tab, none, gridded, st);
 }
 
 cudaError_t launch_domain_stage(const OneDomain &one, int stage, cudaStream_t st) {
     BatchTable tab;
     memset(&tab, 0, sizeof tab);
-    return launch_stage(stage, one.tiles, tab, one, st);
+    return launch_stage(stage, one.tiles, tab, one, one.args.wind.n > 0 && !one.args.clk.wind_uniform, st);
 }
 
 }  // namespace swe
