@@ -81,6 +81,42 @@ def test_split_reaches_the_horizon_like_the_whole_domain(swe):
         assert np.array_equal(a, b)
 
 
+@pytest.fixture(scope="session")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_kahan"])
+def test_split_matches_the_oracle_decomposition(swe, oracle_mod, prec):
+    """The GPU's windows against the FP64 oracle stepped as the same 3 x 2
+    windows (oracle/decomp.py), 300 steps on a coast whose wet corners are
+    at least 5 m deep (no drying fronts to amplify rounding), gridded wind
+    and tide frames sampled at whole-domain positions: the FP32 parity
+    bounds of a whole domain (max |d eta| <= 1e-4 m, relative L2 of the
+    momenta <= 1e-4)."""
+    from oracle import decomp
+    from paper_1912_02457_gb300.split import SplitDomain
+    wl = synth.coastal(120, 84, seed_config=31, dtype=np.float32)
+    wl.wind = gridded_wind(7, 5, hours=3, seed=3)
+    land_corner = wl.H == synth.LAND
+    wl.H = np.where(land_corner, wl.H, np.maximum(wl.H, 5.0)).astype(np.float32)
+    wl.eta = np.zeros_like(wl.eta)
+    (re, ru, rv), (t, _) = decomp.run_split(wl.astype(np.float64), 3, 2, 300)
+    with SplitDomain(wl, 3, 2, prec) as s:
+        s.step(300)
+        e, u, v = s.state()
+        info = s.info()
+
+    def rel_l2(a, b):
+        return float(np.linalg.norm(a.astype(np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    deta = float(np.abs(e.astype(np.float64) - re).max())
+    print("SPLIT_VS_ORACLE", prec, deta, rel_l2(u, ru), rel_l2(v, rv), info.t, t)
+    assert deta <= 1e-4 and rel_l2(u, ru) <= 1e-4 and rel_l2(v, rv) <= 1e-4
+    assert abs(info.t - t) <= 1e-6 * t
+
+
 def test_what_is_not_a_decomposition_is_rejected(swe):
     import ctypes as C
     from paper_1912_02457_gb300.split import SplitDomain
