@@ -704,10 +704,18 @@ static int warp_slots() {
 //
 // A warp item is a strip of 28 output columns by a run of rows
 // [j0, j0 + n), packed as {strip, j0 | n << 16}. A row costs about the same
-// everywhere except in the strips whose two outer lanes are ghosts of a
-// nested edge (they take the edge-state path: ~10% more per row) and, in
-// stage 2, in flow-relaxation zones (~13% more; weights fitted to per-warp
-// times on the coastal 1024 x 1024 step and tuned by measurement); the
+// everywhere except where the march takes the general load path (the
+// strips whose lanes reach past the west or east edge, and the items at the
+// south and north edges: ~17% more per row), in the strips whose outer
+// lanes are ghosts of a nested edge (another ~20%: the edge-state loads)
+// and, in stage 2, in flow-relaxation zones (~8%). The weights are fitted
+// to per-warp times of both stages on the coastal 1024 x 1024 step (per-row
+// cost over an interior row, stage 1 / stage 2: east wall strip 1.20 /
+// 1.16, south and north edge items 1.21 / 1.29, nested west strip 1.38 /
+// 1.43); the earlier weights (ghost strips +10%, relaxation +13%, no
+// general-path term) left the west strip's items ending ~5 us after the
+// median warp of stage 2, and refitting took stage 2 from 38.9 to 36.8 us
+// and the step from 18.1e9 to 18.9e9 cell-updates/s back to back. The
 // four halo rows a march adds cost about a third of a row each. Rows without a wet cell in the
 // strip are left out (land cells are never written and never enter the CFL
 // maximum, and a march recomputes its own halo): each strip falls into
@@ -718,15 +726,19 @@ static int warp_slots() {
 
 namespace {
 
-constexpr int kGhostCost = 10, kFrsCost = 13, kHaloCost = 133;
+constexpr int kNonIntCost = 17, kGhostCost = 20, kFrsCost = 8, kHaloCost = 133;
+constexpr int kEdgeRows = 12;
 
 struct PlanCtx {
     int nx, ny, strips, fw;
     bool nest[4];
     const unsigned char *wet;       // strips x ny, strip-major; NULL: all wet
     bool is_wet(int j, int s) const { return !wet || wet[(size_t)s * ny + j] != 0; }
+    // the strips whose lanes reach past the west or east edge march on the
+    // general load path (ghost handling on every row)
+    bool cols_edge(int s) const { return s * kStrip - 2 < 0 || s * kStrip + 29 >= nx; }
     int strip_extra(int s) const {
-        int c = 0;
+        int c = cols_edge(s) ? kNonIntCost : 0;
         if ((s == 0 && nest[EDGE_W]) || (s == strips - 1 && nest[EDGE_E])) c += kGhostCost;
         const int c0 = s * kStrip, c1 = std::min(c0 + kStrip, nx);
         if ((nest[EDGE_W] && c0 < fw) || (nest[EDGE_E] && c1 > nx - fw)) c += kFrsCost;
@@ -734,7 +746,10 @@ struct PlanCtx {
     }
     int row_cost(int j, int s, int xs) const {
         const bool frs = is_wet(j, s) && ((nest[EDGE_S] && j < fw) || (nest[EDGE_N] && j >= ny - fw));
-        return kPlanUnit + xs + (frs ? kFrsCost : 0);
+        // the first and last item of a strip (about kEdgeRows rows) march on
+        // the general load path too
+        const bool edge = !cols_edge(s) && (j < kEdgeRows || j >= ny - kEdgeRows);
+        return kPlanUnit + xs + (frs ? kFrsCost : 0) + (edge ? kNonIntCost : 0);
     }
 };
 
