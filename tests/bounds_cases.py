@@ -1,7 +1,8 @@
 """Cases run against the bounds-checked library (SWE_LIBRARY points at it):
 tiny odd grids with every boundary kind, land across strips, a spatially
-varying wind, flow relaxation, a batch of mixed domains, both FP32 modes,
-each also with the face-speed time step (its speed pass).
+varying wind, flow relaxation, a batch of mixed domains, windows of a
+decomposed domain, both FP32 modes, each single domain also with the
+face-speed time step (its speed pass).
 Prints one JSON object: case name -> [status of swe_get_info, error_cell]."""
 import json
 import os
@@ -79,6 +80,21 @@ def main():
         b.close()
         for d in ds:
             d.close()
+        # domain decomposition: windows of the coastal domain (own-cell
+        # plans, halo columns, cut edges as walls) and of a nested rough
+        # domain with gridded wind (sampling at whole-domain positions)
+        from paper_1912_02457_gb300.split import SplitDomain
+        for name, wl in cases():
+            if not (name.startswith("coastal") or name == "nested+varying wind 61x90"):
+                continue
+            for px, py in ((2, 2), (3, 1)):
+                s = SplitDomain(wl.astype(np.float32), px, py, prec)
+                s.step(5)
+                for k, d in enumerate(s.doms):
+                    i = d.info(check=False)
+                    st = swe.load().swe_get_info(d.h, swe.C.byref(i))
+                    res[f"split {px}x{py} window {k} {name} {prec}"] = [int(st), int(i.error_cell)]
+                s.close()
     print(json.dumps(res))
 
 

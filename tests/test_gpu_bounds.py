@@ -3,7 +3,8 @@ global access of the FP32 stage kernels checks its offset against its
 buffer's extent, and a violation is skipped and reported (SWE_ERR_BOUNDS,
 source line in error_cell). No case may report one; and a build told that
 the last row of every state plane is out of bounds (the allocation is
-untouched, so nothing outside it is ever touched) must report it."""
+untouched, so nothing outside it is ever touched) must report it for every
+whole domain and for windows of every decomposition."""
 import json
 import os
 import subprocess
@@ -40,7 +41,18 @@ def test_no_access_leaves_its_buffer(debug_lib):
 
 def test_the_checks_catch_a_shrunk_extent(debug_lib):
     res = _run(debug_lib, {"SWE_DEBUG_SHRINK_PLANE_ROWS": "1"})
-    flagged = [v for v in res.values() if v[0] == SWE_ERR_BOUNDS]
-    # every case touches its last row; the reported line lies in the kernel source
-    assert len(flagged) == len(res), res
-    assert all(v[1] > 0 for v in flagged)
+    flagged = {k: v for k, v in res.items() if v[0] == SWE_ERR_BOUNDS}
+    # every whole domain touches its last row; the reported line lies in the
+    # kernel source
+    whole = [k for k in res if not k.startswith("split ")]
+    assert all(k in flagged for k in whole), {k: res[k] for k in whole if k not in flagged}
+    assert all(v[1] > 0 for v in flagged.values())
+    # a window plans its wet own rows only, so one whose top rows are all
+    # land reads no cell of its last row; every decomposition has windows
+    # that do
+    splits = {}
+    for k in res:
+        if k.startswith("split "):
+            w = k.split()
+            splits.setdefault((w[1], " ".join(w[4:])), []).append(k in flagged)
+    assert splits and all(any(v) for v in splits.values()), splits
