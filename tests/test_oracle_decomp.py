@@ -94,6 +94,24 @@ def test_partition_covers_the_domain_once():
         synth.partition(5, 40, 3, 1)
 
 
+def test_window_cuts_the_workload():
+    wl = _workload()
+    parts = synth.partition(wl.nx, wl.ny, 2, 2)
+    p = parts[3]                                  # north-east block: cuts to its south and west
+    w = synth.window(wl, p)
+    x0, x1, y0, y1 = p["win"]
+    assert (w.nx, w.ny) == (x1 - x0, y1 - y0) and w.H.shape == (w.ny + 1, w.nx + 1)
+    assert np.array_equal(w.H, wl.H[y0:y1 + 1, x0:x1 + 1])
+    assert np.array_equal(w.eta, wl.eta[y0:y1, x0:x1]) and np.array_equal(w.f, wl.f[y0:y1, x0:x1])
+    # cut edges become walls, the whole domain's own edges keep their kind
+    assert w.bc == (synth.BC_WALL, wl.bc[1], synth.BC_WALL, wl.bc[3])
+    assert w.boundary is wl.boundary and w.wind is wl.wind
+    per = wl.copy()
+    per.bc = (synth.BC_PERIODIC,) * 4
+    with pytest.raises(ValueError):
+        synth.window(per, p)
+
+
 # ---------------------------------------------------------------------------
 # two gloo ranks, one sub-domain each
 
