@@ -291,8 +291,10 @@ int swe_batch_destroy(swe_batch_handle b);
 
 /* ---- domain decomposition on one device --------------------------------
  * n sub-domains (windows created with whole_nx > 0, see swe_params) whose
- * own cells tile the whole domain exactly once and whose halo cells each
- * lie in another sub-domain's own cells, all on one stream, with the same
+ * own cells tile the whole domain exactly once, whose windows hold two
+ * cells beyond their own cells on every side that does not lie on the
+ * whole domain's edge, and whose halo cells each lie in another
+ * sub-domain's own cells, all on one stream, with the same
  * whole domain, cell size, precision and clock parameters; at most
  * SWE_SPLIT_MAX of them. Both calls are asynchronous on that stream.
  * swe_split_sync: one clock for all of them: the CFL maximum of eq:cfl

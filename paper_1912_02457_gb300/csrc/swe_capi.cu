@@ -1135,6 +1135,15 @@ int split_check(const swe_handle *doms, int n) {
             d->p.dt_fixed != a->p.dt_fixed || d->p.dt_update_every != a->p.dt_update_every)
             return SWE_ERR_INVALID_ARG;
     }
+    for (int i = 0; i < n; i++) {
+        // every own cell's two neighbours on each side lie in the window,
+        // or outside the whole domain (the stencil of a stage)
+        const swe_domain *d = doms[i];
+        const Box o = own_box(d);
+        if ((o.x0 > 0 && d->p.own_x0 < 2) || (o.x1 < d->p.whole_nx && d->nx - d->p.own_x1 < 2) ||
+            (o.y0 > 0 && d->p.own_y0 < 2) || (o.y1 < d->p.whole_ny && d->ny - d->p.own_y1 < 2))
+            return SWE_ERR_INVALID_ARG;
+    }
     long long owned = 0;
     for (int i = 0; i < n; i++) {
         const Box oi = own_box(doms[i]);

@@ -138,6 +138,16 @@ def test_what_is_not_a_decomposition_is_rejected(swe):
         # a whole domain is not a window
         with swe.Domain(wl, "f32") as whole:
             assert step([whole.h.value]) == swe.ERR_INVALID_ARG
+    # windows with a one-cell halo tile the domain but miss the stencil
+    thin = synth.partition(wl.nx, wl.ny, 2, 1, halo=1)
+    ds = [swe.Domain(synth.window(wl, p), "f32", window=(p, wl.nx, wl.ny)) for p in thin]
+    try:
+        arr = (C.c_void_p * 2)(*[d.h.value for d in ds])
+        assert L.swe_split_sync(arr, 2) == swe.ERR_INVALID_ARG
+        assert L.swe_split_step(arr, 2, 1) == swe.ERR_INVALID_ARG
+    finally:
+        for d in ds:
+            d.close()
     part = synth.partition(wl.nx, wl.ny, 2, 1)[0]
     with pytest.raises(swe.SweError) as e:
         swe.Domain(synth.window(wl.astype(np.float64), part), "f64", window=(part, wl.nx, wl.ny))
