@@ -1,7 +1,7 @@
 """Domain decomposition of the scheme on the oracle (CPU): sub-domains that
 exchange a two-cell halo after every RK stage and combine their CFL maxima
-step the whole domain bit for bit, in one process and as two gloo ranks
-that exchange their halos as messages. The stencil of Section 3 reads two
+step the whole domain bit for bit, in one process and as two or four gloo
+ranks that exchange their halos as messages. The stencil of Section 3 reads two
 cells along x and y per stage; eq:cfl's maximum is an exact reduction."""
 import os
 import socket
@@ -180,15 +180,18 @@ def _rank_main(rank, ws, port, px, py, q):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("px,py", [(2, 1), (1, 2)])
-def test_two_gloo_ranks_equal_the_whole_domain(whole, px, py):
+@pytest.mark.parametrize("px,py", [(2, 1), (1, 2), (2, 2)])
+def test_gloo_ranks_equal_the_whole_domain(whole, px, py):
+    # two ranks split along x or y; four ranks in 2 x 2, whose window
+    # corners come from the diagonal neighbour
     import torch.multiprocessing as mp
     from oracle import build
     build()                                  # compiled once, before the ranks start
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, px, py, q)) for r in range(2)]
+    ws = px * py
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, px, py, q)) for r in range(ws)]
     for p in procs:
         p.start()
     got = [q.get(timeout=300) for _ in procs]
