@@ -96,15 +96,21 @@ def local_exchange(subs, which, nx, ny):
             a[...] = w[y0:y1, x0:x1]
 
 
-def step(subs, n, t, courant, exchange, reduce_max=lambda v: v):
+def step(subs, n, t, courant, exchange, reduce_max=lambda v: v, t_end=0.0):
     """n steps of the decomposed scheme from time t; ``exchange(subs,
     which)`` refreshes the halos of ``which`` ("qs" after stage 1, "Q"
     after stage 2), ``reduce_max`` combines a local maximum over all
-    processes. Returns (t, dt of the last step)."""
+    processes. t_end > 0: a forecast horizon, as in the oracle's run (the
+    step that would pass it ends on it, steps past it are no-ops). Returns
+    (t, dt of the last step taken)."""
     dt = 0.0
     for _ in range(n):
+        if t_end > 0.0 and t >= t_end * (1.0 - 1e-14):
+            continue
         speed = reduce_max(max(s.max_speed() for s in subs))
         dt = courant * 0.25 / speed
+        if t_end > 0.0 and t + dt > t_end:
+            dt = t_end - t
         for s in subs:
             s.stage1(t, dt)
         exchange(subs, "qs")
@@ -115,13 +121,13 @@ def step(subs, n, t, courant, exchange, reduce_max=lambda v: v):
     return t, dt
 
 
-def run_split(wl, px, py, n):
+def run_split(wl, px, py, n, t_end=0.0):
     """n steps of ``wl`` split into px x py sub-domains in one process;
     returns the assembled (eta, hu, hv) and (t, dt)."""
     parts = synth.partition(wl.nx, wl.ny, px, py)
     subs = [SubOracle(wl, p) for p in parts]
     t, dt = step(subs, n, wl.t0, wl.params.courant,
-                 lambda ss, w: local_exchange(ss, w, wl.nx, wl.ny))
+                 lambda ss, w: local_exchange(ss, w, wl.nx, wl.ny), t_end=t_end)
     out = [np.zeros((wl.ny, wl.nx)) for _ in range(3)]
     for s in subs:
         x0, x1, y0, y1 = s.part["own"]

@@ -55,6 +55,19 @@ def test_split_equals_whole_bit_for_bit(whole, px, py):
     assert _same(out, whole[0]) and clock == whole[1]
 
 
+def test_split_reaches_a_horizon_like_the_oracle():
+    # the horizon falls inside the steps: the last step is shortened to end
+    # on it and the later ones are no-ops, split or whole, as in orc_run
+    from oracle import Oracle, decomp
+    wl = _workload()
+    t_end = 5.0
+    ref = Oracle(wl).run(STEPS, t_end=t_end)
+    assert ref[3] == t_end
+    for px, py in ((1, 1), (2, 2)):
+        out, (t, _) = decomp.run_split(wl, px, py, STEPS, t_end=t_end)
+        assert t == t_end and _same(out, ref[:3])
+
+
 def test_a_one_cell_halo_is_not_enough(whole, monkeypatch):
     # the stage reads two cells on each side: one halo cell breaks the split
     from oracle import decomp
