@@ -66,3 +66,32 @@ def test_create_rejects_bad_descriptions(built_lib):
     assert L.swe_create_domain(C.byref(d), C.byref(p), None, C.byref(h)) == swe.ERR_INVALID_ARG
     assert L.swe_step(None, 1) == swe.ERR_INVALID_ARG
     assert h.value is None
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every field of the ctypes mirrors sits where a C compiler puts it
+    (gcc on include/swe.h): the parameter, description and info structs
+    cross the boundary by pointer."""
+    from paper_1912_02457_gb300 import swe
+    structs = {"swe_params": swe.Params, "swe_domain_desc": swe.DomainDesc, "swe_info": swe.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "swe.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes_sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def ctypes_sizeof(t):
+    import ctypes
+    return ctypes.sizeof(t)
